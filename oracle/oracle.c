@@ -1,0 +1,768 @@
+/*
+ * oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, single-threaded CPU restatement of the modified Cole
+ * impulse method of Usatyuk, "An Modified Cole's Importance Sampling Method
+ * For Low Error Floor QC-LDPC Codes Construction" (arXiv 2208.05795), used
+ * to check the CUDA library.  Only the test suite, the smoke check and the
+ * bench's CPU-baseline leg may load it; the library never does, and this
+ * file shares no code, header or table with the library.
+ *
+ * Every function states the passage it follows.  Where the paper leaves a
+ * choice open the reading taken is stated beside the code.
+ *
+ * Parity status:
+ *   graph expansion (eqs. 1-2)          pinned (Table II / Table V counts)
+ *   girth, Tanner ball                  pinned (BFS on hand-drawn graphs, Table III caption)
+ *   Tree()/TS(), (a,b), orbit           pinned (Table III TS(2,2)=TS(3,2)=128 by brute force)
+ *   canonical key                       pinned (brute force over all shifts)
+ *   min-sum decoder                     hand-computed iteration trace; codeword fixed point
+ *   sum-product decoder                 exact MAP on a cycle-free code
+ *   bisection                           linear scan on the tiny code
+ *   importance-sampling weights         closed forms (mu = 0, Gaussian moments)
+ * The decoders themselves are not specified by the paper ("our used version
+ * of message passing decoder", Sec. III), so the decoder arithmetic has no
+ * paper pin beyond the substitutes above.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Tanner graph                                                        */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int n, m, E;
+    int Z;          /* circulant size; 0 for a general (non-QC) code */
+    int n_b, m_b;
+    int dvmax, dcmax;
+    int *vdeg, *vadj, *vpos; /* checks of v ascending; vpos = position of v in that check */
+    int *cdeg, *cadj;        /* variable nodes of c ascending */
+    int girth;               /* 0 until computed */
+} og_graph;
+
+static int cmp_int(const void *a, const void *b) {
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+static og_graph *graph_from_edges(int n, int m, int E, const int *ec, const int *ev) {
+    og_graph *g = (og_graph *)calloc(1, sizeof(og_graph));
+    g->n = n; g->m = m; g->E = E;
+    g->vdeg = (int *)calloc(n, sizeof(int));
+    g->cdeg = (int *)calloc(m, sizeof(int));
+    for (int e = 0; e < E; e++) { g->vdeg[ev[e]]++; g->cdeg[ec[e]]++; }
+    g->dvmax = 1; g->dcmax = 1;
+    for (int v = 0; v < n; v++) if (g->vdeg[v] > g->dvmax) g->dvmax = g->vdeg[v];
+    for (int c = 0; c < m; c++) if (g->cdeg[c] > g->dcmax) g->dcmax = g->cdeg[c];
+    g->vadj = (int *)malloc(sizeof(int) * (size_t)n * g->dvmax);
+    g->vpos = (int *)malloc(sizeof(int) * (size_t)n * g->dvmax);
+    g->cadj = (int *)malloc(sizeof(int) * (size_t)m * g->dcmax);
+    int *fv = (int *)calloc(n, sizeof(int)), *fc = (int *)calloc(m, sizeof(int));
+    for (int e = 0; e < E; e++) {
+        g->vadj[ev[e] * g->dvmax + fv[ev[e]]++] = ec[e];
+        g->cadj[ec[e] * g->dcmax + fc[ec[e]]++] = ev[e];
+    }
+    for (int v = 0; v < n; v++) qsort(g->vadj + (size_t)v * g->dvmax, g->vdeg[v], sizeof(int), cmp_int);
+    for (int c = 0; c < m; c++) qsort(g->cadj + (size_t)c * g->dcmax, g->cdeg[c], sizeof(int), cmp_int);
+    for (int v = 0; v < n; v++)
+        for (int i = 0; i < g->vdeg[v]; i++) {
+            int c = g->vadj[v * g->dvmax + i];
+            int p = -1;
+            for (int q = 0; q < g->cdeg[c]; q++) if (g->cadj[c * g->dcmax + q] == v) p = q;
+            g->vpos[v * g->dvmax + i] = p;
+        }
+    free(fv); free(fc);
+    return g;
+}
+
+/* Eqs. 1-2: block (i,j) with exponent a >= 0 is P^a, the identity shifted
+ * right a times, i.e. row r of the block has its 1 in column (r + a) mod Z;
+ * a = -1 is the zero block.  Variable node j*Z+k, check node i*Z+r. */
+og_graph *og_from_qc(int m_b, int n_b, int Z, const int *shifts) {
+    int E = 0;
+    for (int i = 0; i < m_b * n_b; i++) if (shifts[i] >= 0) E += Z;
+    int *ec = (int *)malloc(sizeof(int) * (E ? E : 1)), *ev = (int *)malloc(sizeof(int) * (E ? E : 1));
+    int e = 0;
+    for (int i = 0; i < m_b; i++)
+        for (int j = 0; j < n_b; j++) {
+            int a = shifts[i * n_b + j];
+            if (a < 0) continue;
+            for (int r = 0; r < Z; r++) { ec[e] = i * Z + r; ev[e] = j * Z + (r + a) % Z; e++; }
+        }
+    og_graph *g = graph_from_edges(n_b * Z, m_b * Z, E, ec, ev);
+    g->Z = Z; g->n_b = n_b; g->m_b = m_b;
+    free(ec); free(ev);
+    return g;
+}
+
+/* A general parity-check matrix given by its rows (no automorphism used). */
+og_graph *og_from_csr(int n, int m, const int *row_ptr, const int *col_idx) {
+    int E = row_ptr[m];
+    int *ec = (int *)malloc(sizeof(int) * (E ? E : 1));
+    for (int c = 0; c < m; c++) for (int e = row_ptr[c]; e < row_ptr[c + 1]; e++) ec[e] = c;
+    og_graph *g = graph_from_edges(n, m, E, ec, col_idx);
+    free(ec);
+    return g;
+}
+
+void og_free(og_graph *g) {
+    if (!g) return;
+    free(g->vdeg); free(g->vadj); free(g->vpos); free(g->cdeg); free(g->cadj); free(g);
+}
+
+int og_n(const og_graph *g) { return g->n; }
+int og_m(const og_graph *g) { return g->m; }
+int og_E(const og_graph *g) { return g->E; }
+int og_vdeg(const og_graph *g, int v) { return g->vdeg[v]; }
+int og_cdeg(const og_graph *g, int c) { return g->cdeg[c]; }
+int og_vadj(const og_graph *g, int v, int i) { return g->vadj[v * g->dvmax + i]; }
+int og_cadj(const og_graph *g, int c, int p) { return g->cadj[c * g->dcmax + p]; }
+
+/* Girth: shortest cycle of the Tanner graph, by breadth-first search from
+ * every variable node (every cycle passes through one).  Returns 0 if the
+ * graph has no cycle. */
+int og_girth(og_graph *g) {
+    if (g->girth) return g->girth;
+    int N = g->n + g->m;
+    int *dist = (int *)malloc(sizeof(int) * N), *par = (int *)malloc(sizeof(int) * N);
+    int *queue = (int *)malloc(sizeof(int) * N);
+    int best = 1 << 30;
+    for (int s = 0; s < g->n; s++) {
+        for (int i = 0; i < N; i++) dist[i] = -1;
+        int qh = 0, qt = 0;
+        dist[s] = 0; par[s] = -1; queue[qt++] = s;
+        while (qh < qt) {
+            int u = queue[qh++];
+            if (2 * dist[u] + 1 >= best) break;
+            int deg = u < g->n ? g->vdeg[u] : g->cdeg[u - g->n];
+            for (int k = 0; k < deg; k++) {
+                int w = u < g->n ? g->n + g->vadj[u * g->dvmax + k] : g->cadj[(u - g->n) * g->dcmax + k];
+                if (w == par[u]) continue;
+                if (dist[w] < 0) { dist[w] = dist[u] + 1; par[w] = u; queue[qt++] = w; }
+                else if (dist[u] + dist[w] + 1 < best) best = dist[u] + dist[w] + 1;
+            }
+        }
+    }
+    free(dist); free(par); free(queue);
+    g->girth = best == (1 << 30) ? 0 : best;
+    return g->girth;
+}
+
+/* Tanner ball: the variable nodes other than v reached from v along
+ * VN-CN-VN or VN-CN-VN-CN-VN, i.e. the variable layers of the depth-3
+ * unrolled tree VN1-CN1-VN2-CN2-VN3 of Sec. III (Fig. 3).  Ascending. */
+int og_ball4(const og_graph *g, int v, int *out) {
+    unsigned char *seen = (unsigned char *)calloc(g->n, 1);
+    seen[v] = 1;
+    int cnt = 0;
+    for (int i = 0; i < g->vdeg[v]; i++) {
+        int c = g->vadj[v * g->dvmax + i];
+        for (int p = 0; p < g->cdeg[c]; p++) {
+            int u = g->cadj[c * g->dcmax + p];
+            if (!seen[u]) { seen[u] = 1; out[cnt++] = u; }
+        }
+    }
+    int d2 = cnt;
+    for (int t = 0; t < d2; t++) {
+        int u = out[t];
+        for (int i = 0; i < g->vdeg[u]; i++) {
+            int c = g->vadj[u * g->dvmax + i];
+            for (int p = 0; p < g->cdeg[c]; p++) {
+                int w = g->cadj[c * g->dcmax + p];
+                if (!seen[w]) { seen[w] = 1; out[cnt++] = w; }
+            }
+        }
+    }
+    free(seen);
+    qsort(out, cnt, sizeof(int), cmp_int);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------ */
+/* Canonical form under the circulant shift (graph automorphism)       */
+/* ------------------------------------------------------------------ */
+
+/* Shifting every variable node (j,k) to (j,(k+s) mod Z) (and every check
+ * likewise) maps the QC Tanner graph onto itself (Sec. III: "graph
+ * automorphism"; Table III counts are multiples of Z = 128).  The key of a
+ * set T is the lexicographically smallest sorted tuple among the shifts by
+ * s = -(v mod Z), v in T; a general code uses the sorted set itself.  The
+ * orbit size is Z / |{s in [0,Z): T + s = T}|.  Returns the orbit size. */
+static int lex_less(const int *a, const int *b, int n) {
+    for (int i = 0; i < n; i++) if (a[i] != b[i]) return a[i] < b[i];
+    return 0;
+}
+
+int og_canon(const og_graph *g, const int *T, int a, int *key) {
+    if (a == 0) return 1;
+    if (g->Z == 0) {
+        memcpy(key, T, sizeof(int) * a);
+        qsort(key, a, sizeof(int), cmp_int);
+        return 1;
+    }
+    int Z = g->Z;
+    int *tmp = (int *)malloc(sizeof(int) * a), *base = (int *)malloc(sizeof(int) * a);
+    memcpy(base, T, sizeof(int) * a);
+    qsort(base, a, sizeof(int), cmp_int);
+    int have = 0;
+    for (int t = 0; t < a; t++) {
+        int s = (Z - T[t] % Z) % Z;
+        for (int i = 0; i < a; i++) tmp[i] = (T[i] / Z) * Z + (T[i] % Z + s) % Z;
+        qsort(tmp, a, sizeof(int), cmp_int);
+        if (!have || lex_less(tmp, key, a)) { memcpy(key, tmp, sizeof(int) * a); have = 1; }
+    }
+    int stab = 0;
+    for (int s = 0; s < Z; s++) {
+        for (int i = 0; i < a; i++) tmp[i] = (T[i] / Z) * Z + (T[i] % Z + s) % Z;
+        qsort(tmp, a, sizeof(int), cmp_int);
+        if (memcmp(tmp, base, sizeof(int) * a) == 0) stab++;
+    }
+    free(tmp); free(base);
+    return Z / stab;
+}
+
+/* ------------------------------------------------------------------ */
+/* Candidate impulse sets                                              */
+/* ------------------------------------------------------------------ */
+
+/* Sec. III: for each orbit representative VN (QC: (j,0); general: every
+ * VN), impulse sets are drawn from the depth-3 tree around it.  Reading:
+ * a set contains the representative and at most max_size-1 other nodes of
+ * its Tanner ball; with cycle_len = 2l > 0 the variable-node sets of the
+ * 2l-cycles through the representative are added.  Every set is reduced to
+ * its canonical key and duplicates are dropped. */
+typedef struct { int size; int v[4]; } og_cand;
+
+static int cmp_cand(const void *pa, const void *pb) {
+    const og_cand *a = (const og_cand *)pa, *b = (const og_cand *)pb;
+    if (a->size != b->size) return a->size < b->size ? -1 : 1;
+    for (int i = 0; i < a->size; i++) if (a->v[i] != b->v[i]) return a->v[i] < b->v[i] ? -1 : 1;
+    return 0;
+}
+
+typedef struct { og_cand *c; size_t n, cap; } cand_vec;
+
+static void cv_push(const og_graph *g, cand_vec *cv, const int *vars, int size) {
+    if (cv->n == cv->cap) {
+        cv->cap = cv->cap ? 2 * cv->cap : 1024;
+        cv->c = (og_cand *)realloc(cv->c, sizeof(og_cand) * cv->cap);
+    }
+    og_cand *o = &cv->c[cv->n++];
+    o->size = size;
+    int key[4];
+    og_canon(g, vars, size, key);
+    for (int i = 0; i < 4; i++) o->v[i] = i < size ? key[i] : -1;
+}
+
+/* all simple cycles of length 2l through variable node v0, as VN sets */
+static void cycles_from(const og_graph *g, int v0, int l, int depth, int *vs, int *cs,
+                        cand_vec *cv) {
+    int v = vs[depth];
+    for (int i = 0; i < g->vdeg[v]; i++) {
+        int c = g->vadj[v * g->dvmax + i];
+        int used = 0;
+        for (int t = 0; t < depth; t++) if (cs[t] == c) used = 1;
+        if (used) continue;
+        for (int p = 0; p < g->cdeg[c]; p++) {
+            int u = g->cadj[c * g->dcmax + p];
+            if (u == v) continue;
+            if (depth == l - 1) {
+                if (u == v0) { cs[depth] = c; cv_push(g, cv, vs, l); }
+                continue;
+            }
+            int dup = 0;
+            for (int t = 0; t <= depth; t++) if (vs[t] == u) dup = 1;
+            if (dup) continue;
+            cs[depth] = c; vs[depth + 1] = u;
+            cycles_from(g, v0, l, depth + 1, vs, cs, cv);
+        }
+    }
+}
+
+typedef struct { og_cand *c; size_t n; } og_cands;
+
+og_cands *og_candidates(const og_graph *g, int max_size, int cycle_len) {
+    cand_vec cv = {0};
+    int *ball = (int *)malloc(sizeof(int) * g->n);
+    int nrep = g->Z ? g->n_b : g->n;
+    for (int r = 0; r < nrep; r++) {
+        int v0 = g->Z ? r * g->Z : r;
+        int B = og_ball4(g, v0, ball);
+        int s[4] = {v0, 0, 0, 0};
+        if (max_size >= 1) cv_push(g, &cv, s, 1);
+        for (int i = 0; i < B && max_size >= 2; i++) {
+            s[1] = ball[i];
+            cv_push(g, &cv, s, 2);
+            for (int j = i + 1; j < B && max_size >= 3; j++) {
+                s[2] = ball[j];
+                cv_push(g, &cv, s, 3);
+                for (int k = j + 1; k < B && max_size >= 4; k++) { s[3] = ball[k]; cv_push(g, &cv, s, 4); }
+            }
+        }
+        if (cycle_len >= 4 && cycle_len <= 8) {
+            int vs[4] = {v0, 0, 0, 0}, cs[4];
+            cycles_from(g, v0, cycle_len / 2, 0, vs, cs, &cv);
+        }
+    }
+    free(ball);
+    qsort(cv.c, cv.n, sizeof(og_cand), cmp_cand);
+    size_t u = 0;
+    for (size_t i = 0; i < cv.n; i++)
+        if (u == 0 || cmp_cand(&cv.c[u - 1], &cv.c[i]) != 0) cv.c[u++] = cv.c[i];
+    og_cands *out = (og_cands *)malloc(sizeof(og_cands));
+    out->c = cv.c; out->n = u;
+    return out;
+}
+
+size_t og_cands_count(const og_cands *c) { return c->n; }
+void og_cands_copy(const og_cands *c, int *out /* n x 5: size, v0..v3 */) {
+    for (size_t i = 0; i < c->n; i++) {
+        out[5 * i] = c->c[i].size;
+        for (int k = 0; k < 4; k++) out[5 * i + 1 + k] = c->c[i].v[k];
+    }
+}
+void og_cands_free(og_cands *c) { if (c) { free(c->c); free(c); } }
+
+/* ------------------------------------------------------------------ */
+/* Decoders                                                            */
+/* ------------------------------------------------------------------ */
+
+static int clampi(int x, int lo, int hi) { return x < lo ? lo : x > hi ? hi : x; }
+static float clampf(float x, float lo, float hi) { return x < lo ? lo : x > hi ? hi : x; }
+
+static int unsat_count(const og_graph *g, const unsigned char *x) {
+    int u = 0;
+    for (int c = 0; c < g->m; c++) {
+        int par = 0;
+        for (int p = 0; p < g->cdeg[c]; p++) par ^= x[g->cadj[c * g->dcmax + p]];
+        u += par;
+    }
+    return u;
+}
+
+/* Fixed-point normalized min-sum, flooding schedule (the decoder of the
+ * enumeration is left open by the paper, Sec. III; this is the int16
+ * decoder of the workload definition).
+ *   start:  q(v->c) = L_v;  x_0 = [L_v < 0]
+ *   check:  r(c->v) = s * ((an * m) >> as), m = min over v' != v of |q(v'->c)|,
+ *           s = product over v' != v of sgn q(v'->c), sgn(0) = +1
+ *   var:    P_v = L_v + sum_c r(c->v);  q(v->c) = clamp(P_v - r(c->v), -sat, sat);
+ *           x_v = [P_v < 0]
+ *   u_k = number of unsatisfied checks of x_k (w_H(H x_k), Sec. III); stop at
+ *   the first k with u_k = 0, else after K iterations (K_last = k).
+ * Best error pattern (Sec. III, S(min_iter w_H(H x_iter)) with the list
+ * starting at x_{floor(girth/2)}): x* = x_k for the first k in
+ * [wstart, K_last] with minimal u_k; if K_last < wstart, x* = x_{K_last}.
+ * Returns 1 if the decoder failed (x_{K_last} != 0), else 0. */
+int og_decode_nms(const og_graph *g, const int *L, int K, int sat, int an, int as, int wstart,
+                  unsigned char *xbest, int *K_last, int *u_trace /* K+1 or NULL */,
+                  int *P_out /* n or NULL: P_v after the last iteration run */) {
+    int E = g->m * g->dcmax;
+    int *q = (int *)malloc(sizeof(int) * E), *r = (int *)malloc(sizeof(int) * E);
+    unsigned char *x = (unsigned char *)malloc(g->n);
+    for (int v = 0; v < g->n; v++) {
+        if (P_out) P_out[v] = L[v];
+        x[v] = L[v] < 0;
+        for (int i = 0; i < g->vdeg[v]; i++)
+            q[g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i]] = L[v];
+    }
+    int u = unsat_count(g, x), ubest = 1 << 30, kl = 0;
+    if (u_trace) u_trace[0] = u;
+    for (int k = 1; k <= K && u != 0; k++) {
+        for (int c = 0; c < g->m; c++) {
+            int d = g->cdeg[c];
+            for (int p = 0; p < d; p++) {
+                int mn = 1 << 30, sg = 1;
+                for (int p2 = 0; p2 < d; p2++) {
+                    if (p2 == p) continue;
+                    int qq = q[c * g->dcmax + p2];
+                    int mag = qq < 0 ? -qq : qq;
+                    if (mag < mn) mn = mag;
+                    if (qq < 0) sg = -sg;
+                }
+                if (d == 1) mn = sat; /* no other edge: the check alone forces 0 */
+                r[c * g->dcmax + p] = sg * ((an * mn) >> as);
+            }
+        }
+        for (int v = 0; v < g->n; v++) {
+            int P = L[v];
+            for (int i = 0; i < g->vdeg[v]; i++)
+                P += r[g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i]];
+            for (int i = 0; i < g->vdeg[v]; i++) {
+                int e = g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i];
+                q[e] = clampi(P - r[e], -sat, sat);
+            }
+            x[v] = P < 0;
+            if (P_out) P_out[v] = P;
+        }
+        u = unsat_count(g, x);
+        if (u_trace) u_trace[k] = u;
+        kl = k;
+        if (k >= wstart && u < ubest) { ubest = u; memcpy(xbest, x, g->n); }
+    }
+    if (kl < wstart) memcpy(xbest, x, g->n);
+    int fail = 0;
+    for (int v = 0; v < g->n; v++) fail |= x[v];
+    *K_last = kl;
+    free(q); free(r); free(x);
+    return fail;
+}
+
+/* Floating-point sum-product (same flooding schedule and stopping rule).
+ *   check:  r(c->v) = 2 atanh( prod over v' != v, ascending, of tanh(q(v'->c)/2) ),
+ *           +-clip when |prod| >= 1, then clipped to [-clip, clip]
+ *   var:    P_v = L_v + r(c_0->v) + r(c_1->v) + ... (checks ascending);
+ *           q(v->c) = clip(P_v - r(c->v)); x_v = [P_v < 0]
+ * Single precision, as the workload states. */
+int og_decode_spa(const og_graph *g, const float *L, int K, float clip, int wstart,
+                  unsigned char *xbest, int *K_last, int *u_trace) {
+    int E = g->m * g->dcmax;
+    float *q = (float *)malloc(sizeof(float) * E), *r = (float *)malloc(sizeof(float) * E);
+    float *t = (float *)malloc(sizeof(float) * g->dcmax);
+    unsigned char *x = (unsigned char *)malloc(g->n);
+    for (int v = 0; v < g->n; v++) {
+        x[v] = L[v] < 0.0f;
+        for (int i = 0; i < g->vdeg[v]; i++)
+            q[g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i]] = L[v];
+    }
+    int u = unsat_count(g, x), ubest = 1 << 30, kl = 0;
+    if (u_trace) u_trace[0] = u;
+    for (int k = 1; k <= K && u != 0; k++) {
+        for (int c = 0; c < g->m; c++) {
+            int d = g->cdeg[c];
+            for (int p = 0; p < d; p++) t[p] = tanhf(q[c * g->dcmax + p] * 0.5f);
+            for (int p = 0; p < d; p++) {
+                float prod = 1.0f;
+                for (int p2 = 0; p2 < d; p2++) if (p2 != p) prod = prod * t[p2];
+                float rr;
+                if (fabsf(prod) >= 1.0f) rr = prod > 0.0f ? clip : -clip;
+                else rr = 2.0f * atanhf(prod);
+                r[c * g->dcmax + p] = clampf(rr, -clip, clip);
+            }
+        }
+        for (int v = 0; v < g->n; v++) {
+            float P = L[v];
+            for (int i = 0; i < g->vdeg[v]; i++)
+                P = P + r[g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i]];
+            for (int i = 0; i < g->vdeg[v]; i++) {
+                int e = g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i];
+                q[e] = clampf(P - r[e], -clip, clip);
+            }
+            x[v] = P < 0.0f;
+        }
+        u = unsat_count(g, x);
+        if (u_trace) u_trace[k] = u;
+        kl = k;
+        if (k >= wstart && u < ubest) { ubest = u; memcpy(xbest, x, g->n); }
+    }
+    if (kl < wstart) memcpy(xbest, x, g->n);
+    int fail = 0;
+    for (int v = 0; v < g->n; v++) fail |= x[v];
+    *K_last = kl;
+    free(q); free(r); free(t); free(x);
+    return fail;
+}
+
+/* Exact posterior-LLR sum-product output on the final iteration, for
+ * tests on cycle-free codes: returns P_v after exactly K iterations
+ * without early stopping. */
+void og_spa_posterior(const og_graph *g, const float *L, int K, float clip, float *P_out) {
+    int E = g->m * g->dcmax;
+    float *q = (float *)malloc(sizeof(float) * E), *r = (float *)malloc(sizeof(float) * E);
+    float *t = (float *)malloc(sizeof(float) * g->dcmax);
+    for (int v = 0; v < g->n; v++) {
+        P_out[v] = L[v];
+        for (int i = 0; i < g->vdeg[v]; i++)
+            q[g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i]] = L[v];
+    }
+    for (int k = 1; k <= K; k++) {
+        for (int c = 0; c < g->m; c++) {
+            int d = g->cdeg[c];
+            for (int p = 0; p < d; p++) t[p] = tanhf(q[c * g->dcmax + p] * 0.5f);
+            for (int p = 0; p < d; p++) {
+                float prod = 1.0f;
+                for (int p2 = 0; p2 < d; p2++) if (p2 != p) prod = prod * t[p2];
+                float rr;
+                if (fabsf(prod) >= 1.0f) rr = prod > 0.0f ? clip : -clip;
+                else rr = 2.0f * atanhf(prod);
+                r[c * g->dcmax + p] = clampf(rr, -clip, clip);
+            }
+        }
+        for (int v = 0; v < g->n; v++) {
+            float P = L[v];
+            for (int i = 0; i < g->vdeg[v]; i++)
+                P = P + r[g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i]];
+            for (int i = 0; i < g->vdeg[v]; i++) {
+                int e = g->vadj[v * g->dvmax + i] * g->dcmax + g->vpos[v * g->dvmax + i];
+                q[e] = clampf(P - r[e], -clip, clip);
+            }
+            P_out[v] = P;
+        }
+    }
+    free(q); free(r); free(t);
+}
+
+/* ------------------------------------------------------------------ */
+/* Trapping-set extraction (Sec. III, S1/S2 sieving)                   */
+/* ------------------------------------------------------------------ */
+
+/* |N(c) cap S| for the indicator S */
+static int check_count(const og_graph *g, int c, const unsigned char *S) {
+    int k = 0;
+    for (int p = 0; p < g->cdeg[c]; p++) k += S[g->cadj[c * g->dcmax + p]];
+    return k;
+}
+
+/* Tree(S): the largest subset of S whose induced subgraph has no tree-like
+ * part, i.e. the variable nodes of the 2-core of the bipartite graph on S
+ * and N(S): checks with at most one neighbour in the set and variable nodes
+ * with at most one remaining check are deleted until none is left.  In place. */
+void og_tree(const og_graph *g, unsigned char *S) {
+    int changed = 1;
+    while (changed) {
+        changed = 0;
+        for (int v = 0; v < g->n; v++) {
+            if (!S[v]) continue;
+            int live = 0;
+            for (int i = 0; i < g->vdeg[v]; i++)
+                if (check_count(g, g->vadj[v * g->dvmax + i], S) >= 2) live++;
+            if (live < 2) { S[v] = 0; changed = 1; }
+        }
+    }
+}
+
+/* TS(S): S together with every variable node outside S that has at least
+ * two checks in N(S), i.e. closes a new cycle with S (one pass). */
+void og_ts_closure(const og_graph *g, const unsigned char *S, unsigned char *out) {
+    unsigned char *inN = (unsigned char *)calloc(g->m, 1);
+    for (int c = 0; c < g->m; c++) inN[c] = check_count(g, c, S) >= 1;
+    for (int v = 0; v < g->n; v++) {
+        out[v] = S[v];
+        if (S[v]) continue;
+        int k = 0;
+        for (int i = 0; i < g->vdeg[v]; i++) k += inN[g->vadj[v * g->dvmax + i]];
+        if (k >= 2) out[v] = 1;
+    }
+    free(inN);
+}
+
+/* TS(a,b) of Sec. II: a = |T|, b = number of checks with an odd number of
+ * neighbours in T.  *elem = 1 if every check touching T touches it at most
+ * twice (an elementary set). */
+void og_classify(const og_graph *g, const unsigned char *T, int *a, int *b, int *elem) {
+    int aa = 0, bb = 0, el = 1;
+    for (int v = 0; v < g->n; v++) aa += T[v];
+    for (int c = 0; c < g->m; c++) {
+        int k = check_count(g, c, T);
+        if (k & 1) bb++;
+        if (k > 2) el = 0;
+    }
+    *a = aa; *b = bb; *elem = el;
+}
+
+/* Sieving (Sec. III): with X = supp(x*) cup I, take S1 = Tree(X) if it is
+ * not empty, else S2 = Tree(TS(X)).  Returns 1 (S1), 2 (S2) or 0 (both
+ * empty: an acyclic failure, not a trapping set).  T receives the set. */
+int og_extract(const og_graph *g, const unsigned char *xstar, const int *I, int nI,
+               unsigned char *T) {
+    unsigned char *X = (unsigned char *)malloc(g->n);
+    memcpy(X, xstar, g->n);
+    for (int t = 0; t < nI; t++) X[I[t]] = 1;
+    memcpy(T, X, g->n);
+    og_tree(g, T);
+    int which = 1, any = 0;
+    for (int v = 0; v < g->n; v++) any |= T[v];
+    if (!any) {
+        og_ts_closure(g, X, T);
+        og_tree(g, T);
+        which = 2;
+        any = 0;
+        for (int v = 0; v < g->n; v++) any |= T[v];
+        if (!any) which = 0;
+    }
+    free(X);
+    return which;
+}
+
+/* ------------------------------------------------------------------ */
+/* The enumeration: impulse, bisection, extraction, canonical dedupe    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int decoder;    /* 0 = fixed-point min-sum, 1 = float sum-product */
+    int K;
+    int base_llr;   /* fixed point, units of 1/8 */
+    int sat;        /* fixed-point message and channel saturation */
+    int alpha_num, alpha_shift;
+    int amp_steps;  /* s */
+    float spa_clip; /* sum-product clip */
+    float spa_amax; /* sum-product: amplitude range in LLR units */
+} og_params;
+
+typedef struct {
+    int a, b, orbit, elem, count, kind;
+    int thr;        /* min threshold (fixed point) */
+    float thr_f;    /* min threshold (float) */
+    int *key;
+} og_ts;
+
+typedef struct {
+    /* per candidate */
+    size_t ncand;
+    int *thr;       /* -1 = no failure up to the largest amplitude */
+    float *thr_f;
+    int *ts;        /* index into the sorted TS list, -1 if none */
+    int *which;     /* 0 none / acyclic, 1 = S1, 2 = S2 */
+    int *decodes, *iters;
+    /* distinct trapping sets sorted by (a, b, key) */
+    int nts;
+    og_ts *list;
+} og_result;
+
+typedef struct { int a, b, orbit, elem, kind, thr, cand; float thr_f; int *key; } ts_hit;
+
+static int cmp_hit(const void *pa, const void *pb) {
+    const ts_hit *x = (const ts_hit *)pa, *y = (const ts_hit *)pb;
+    if (x->a != y->a) return x->a < y->a ? -1 : 1;
+    if (x->b != y->b) return x->b < y->b ? -1 : 1;
+    for (int i = 0; i < x->a; i++) if (x->key[i] != y->key[i]) return x->key[i] < y->key[i] ? -1 : 1;
+    return 0;
+}
+
+/* The impulse of Sec. III: the impulse nodes get h(1 - eps) and all others
+ * keep h.  Reading: in fixed point L_v = sat(base - A) on I and base
+ * elsewhere, A = eps * h in units of 1/8; in float L_v = clip(base/8 -
+ * eps * amax) on I.  The amplitude is bisected: A = 2^s - 1 first (no
+ * failure there means no threshold), then up to s halvings of [lo, hi]
+ * keeping the failing end; the threshold is the final hi and the trapping
+ * set comes from the decode at that hi. */
+og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* ncand x 5 */,
+                        size_t ncand) {
+    int girth = og_girth(g);
+    int wstart = girth / 2 > 1 ? girth / 2 : 1;
+    og_result *R = (og_result *)calloc(1, sizeof(og_result));
+    R->ncand = ncand;
+    R->thr = (int *)malloc(sizeof(int) * ncand);
+    R->thr_f = (float *)malloc(sizeof(float) * ncand);
+    R->ts = (int *)malloc(sizeof(int) * ncand);
+    R->which = (int *)malloc(sizeof(int) * ncand);
+    R->decodes = (int *)malloc(sizeof(int) * ncand);
+    R->iters = (int *)malloc(sizeof(int) * ncand);
+    ts_hit *hits = (ts_hit *)malloc(sizeof(ts_hit) * (ncand ? ncand : 1));
+    size_t nh = 0;
+    int *Li = (int *)malloc(sizeof(int) * g->n);
+    float *Lf = (float *)malloc(sizeof(float) * g->n);
+    unsigned char *xb = (unsigned char *)malloc(g->n), *keep = (unsigned char *)malloc(g->n);
+    unsigned char *T = (unsigned char *)malloc(g->n);
+    int *tv = (int *)malloc(sizeof(int) * g->n);
+    for (size_t ci = 0; ci < ncand; ci++) {
+        int nI = cands[5 * ci];
+        const int *I = cands + 5 * ci + 1;
+        int decodes = 0, iters = 0, kl, failed = 0;
+        int thr = -1;
+        float thr_f = -1.0f;
+        if (pp->decoder == 0) {
+            int lo = 0, hi = (1 << pp->amp_steps) - 1;
+            for (int v = 0; v < g->n; v++) Li[v] = clampi(pp->base_llr, -pp->sat, pp->sat);
+            for (int t = 0; t < nI; t++) Li[I[t]] = clampi(pp->base_llr - hi, -pp->sat, pp->sat);
+            int f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL, NULL);
+            decodes++; iters += kl;
+            if (f) {
+                failed = 1; memcpy(keep, xb, g->n);
+                for (int st = 0; st < pp->amp_steps && hi - lo > 1; st++) {
+                    int mid = (lo + hi) >> 1;
+                    for (int t = 0; t < nI; t++) Li[I[t]] = clampi(pp->base_llr - mid, -pp->sat, pp->sat);
+                    f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL, NULL);
+                    decodes++; iters += kl;
+                    if (f) { hi = mid; memcpy(keep, xb, g->n); } else lo = mid;
+                }
+                thr = hi;
+            }
+        } else {
+            float lo = 0.0f, hi = 1.0f, base = (float)pp->base_llr / 8.0f;
+            for (int v = 0; v < g->n; v++) Lf[v] = clampf(base, -pp->spa_clip, pp->spa_clip);
+            for (int t = 0; t < nI; t++) Lf[I[t]] = clampf(base - hi * pp->spa_amax, -pp->spa_clip, pp->spa_clip);
+            int f = og_decode_spa(g, Lf, pp->K, pp->spa_clip, wstart, xb, &kl, NULL);
+            decodes++; iters += kl;
+            if (f) {
+                failed = 1; memcpy(keep, xb, g->n);
+                for (int st = 0; st < pp->amp_steps; st++) {
+                    float mid = 0.5f * (lo + hi);
+                    for (int t = 0; t < nI; t++) Lf[I[t]] = clampf(base - mid * pp->spa_amax, -pp->spa_clip, pp->spa_clip);
+                    f = og_decode_spa(g, Lf, pp->K, pp->spa_clip, wstart, xb, &kl, NULL);
+                    decodes++; iters += kl;
+                    if (f) { hi = mid; memcpy(keep, xb, g->n); } else lo = mid;
+                }
+                thr_f = hi;
+            }
+        }
+        R->thr[ci] = thr; R->thr_f[ci] = thr_f;
+        R->decodes[ci] = decodes; R->iters[ci] = iters;
+        R->ts[ci] = -1; R->which[ci] = 0;
+        if (!failed) continue;
+        int which = og_extract(g, keep, I, nI, T);
+        R->which[ci] = which;
+        if (!which) continue;
+        int a = 0, b, el;
+        for (int v = 0; v < g->n; v++) if (T[v]) tv[a++] = v;
+        og_classify(g, T, &a, &b, &el);
+        ts_hit *h = &hits[nh++];
+        h->a = a; h->b = b; h->elem = el; h->kind = which; h->thr = thr; h->thr_f = thr_f;
+        h->cand = (int)ci;
+        h->key = (int *)malloc(sizeof(int) * a);
+        h->orbit = og_canon(g, tv, a, h->key);
+    }
+    qsort(hits, nh, sizeof(ts_hit), cmp_hit);
+    R->list = (og_ts *)malloc(sizeof(og_ts) * (nh ? nh : 1));
+    int nts = 0;
+    size_t head = 0; /* first hit of the current group */
+    for (size_t i = 0; i < nh; i++) {
+        if (nts == 0 || cmp_hit(&hits[i], &hits[head]) != 0) {
+            head = i;
+            og_ts *t = &R->list[nts++];
+            t->a = hits[i].a; t->b = hits[i].b; t->orbit = hits[i].orbit; t->elem = hits[i].elem;
+            t->kind = hits[i].kind; t->count = 0; t->thr = hits[i].thr; t->thr_f = hits[i].thr_f;
+            t->key = hits[i].key;
+        }
+        og_ts *t = &R->list[nts - 1];
+        t->count++;
+        if (hits[i].thr < t->thr) t->thr = hits[i].thr;
+        if (hits[i].thr_f < t->thr_f) t->thr_f = hits[i].thr_f;
+        R->ts[hits[i].cand] = nts - 1;
+    }
+    for (size_t i = 0, k = 0; i < nh; i++) { /* free the keys not kept in the list */
+        if (k < (size_t)nts && R->list[k].key == hits[i].key) { k++; continue; }
+        free(hits[i].key);
+    }
+    R->nts = nts;
+    free(hits); free(Li); free(Lf); free(xb); free(keep); free(T); free(tv);
+    return R;
+}
+
+int og_res_nts(const og_result *R) { return R->nts; }
+void og_res_cand(const og_result *R, int *thr, float *thr_f, int *ts, int *which, int *decodes, int *iters) {
+    memcpy(thr, R->thr, sizeof(int) * R->ncand);
+    memcpy(thr_f, R->thr_f, sizeof(float) * R->ncand);
+    memcpy(ts, R->ts, sizeof(int) * R->ncand);
+    memcpy(which, R->which, sizeof(int) * R->ncand);
+    memcpy(decodes, R->decodes, sizeof(int) * R->ncand);
+    memcpy(iters, R->iters, sizeof(int) * R->ncand);
+}
+/* info: a, b, orbit, elem, count, thr, kind; returns a */
+int og_res_ts(const og_result *R, int i, int *info, float *thr_f, int *key) {
+    const og_ts *t = &R->list[i];
+    info[0] = t->a; info[1] = t->b; info[2] = t->orbit; info[3] = t->elem;
+    info[4] = t->count; info[5] = t->thr; info[6] = t->kind;
+    *thr_f = t->thr_f;
+    if (key) memcpy(key, t->key, sizeof(int) * t->a);
+    return t->a;
+}
+void og_res_free(og_result *R) {
+    if (!R) return;
+    for (int i = 0; i < R->nts; i++) free(R->list[i].key);
+    free(R->list); free(R->thr); free(R->thr_f); free(R->ts); free(R->which);
+    free(R->decodes); free(R->iters); free(R);
+}
