@@ -1,0 +1,201 @@
+/*
+ * tsx.h -- C ABI of the GB300 trapping-set enumeration library.
+ *
+ * The library implements the data-parallel hot path of the modified Cole
+ * importance-sampling method (V. Usatyuk, arXiv 2208.05795, Sec. III):
+ * impulse-perturbed message-passing decodes of the all-zero codeword on a
+ * QC-LDPC (or general LDPC) Tanner graph, a bisection on the impulse
+ * amplitude, extraction of the failing pattern's cycle-closed core as an
+ * (a,b) trapping set, reduction to one canonical form per circulant-shift
+ * orbit, and deduplication.  Every step runs in CUDA kernels for sm_103a.
+ *
+ * Conventions for every entry point:
+ *   - The return value is TSX_OK (0) or a negative TSX_E* status; no
+ *     exception or process exit crosses this boundary.
+ *   - Input arrays are borrowed for the duration of the call and copied
+ *     where they are kept; output objects are owned by the library until
+ *     the matching free_* call.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Host pointers are plain pageable or pinned memory.
+ *   - Calls on one object are not thread-safe; distinct objects may be used
+ *     from distinct threads.
+ */
+#ifndef TSX_H
+#define TSX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TSX_API __attribute__((visibility("default")))
+#else
+#define TSX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define TSX_OK 0
+#define TSX_EINVAL (-1)       /* bad argument or malformed code description */
+#define TSX_ENOMEM (-2)       /* device or host allocation failed, or a table overflowed */
+#define TSX_ECUDA (-3)        /* a CUDA runtime call failed */
+#define TSX_ETIMEDOUT (-4)    /* a bounded device-side wait ran out */
+#define TSX_EBUSY (-5)        /* resource in use (server admission) */
+#define TSX_EUNSUPPORTED (-6) /* a degree or size above the compiled limits */
+#define TSX_ENOTFOUND (-7)    /* unknown job id */
+#define TSX_EAGAIN (-8)       /* job not finished yet */
+
+/* Human-readable text for a status code (static storage). */
+TSX_API const char *tsx_strerror(int status);
+
+/* Compiled limits. */
+#define TSX_MAX_DC 32    /* check-node degree */
+#define TSX_MAX_DV 16    /* variable-node degree */
+#define TSX_MAX_NB 64    /* QC base-matrix columns */
+#define TSX_MAX_N 32767  /* variable nodes per code */
+
+/* ---- codes (Sec. II, eqs. 1-3) --------------------------------------- */
+typedef struct tsx_code tsx_code;
+
+enum { TSX_CODE_QC = 0, TSX_CODE_CSR = 1 };
+
+/* Description of a parity-check matrix.
+ *   QC (eqs. 1-3): `shifts` is the m_b x n_b exponent matrix E(H),
+ *     row-major, entries in {-1, 0, ..., Z-1}; -1 is the zero block and
+ *     a >= 0 the circulant P^a whose row r has its 1 in column (r+a) mod Z.
+ *     Variable node j*Z+k, check node i*Z+r.  Orbit representatives of the
+ *     circulant-shift automorphism are the variable nodes j*Z.
+ *   CSR: a general matrix by rows: row_ptr[m+1], col_idx[row_ptr[m]] with
+ *     the variable nodes of each check, no duplicates.  No automorphism is
+ *     used: every variable node is a representative. */
+typedef struct {
+    int32_t kind;           /* TSX_CODE_QC or TSX_CODE_CSR */
+    int32_t m_b, n_b, Z;    /* QC */
+    const int32_t *shifts;  /* QC, host */
+    int32_t n, m;           /* CSR */
+    const int32_t *row_ptr; /* CSR, host */
+    const int32_t *col_idx; /* CSR, host */
+} tsx_code_desc;
+
+typedef struct {
+    int32_t kind, n, m, E, Z, n_b, m_b;
+    int32_t dv_max, dc_max;
+    int32_t girth;       /* 0 if the graph has no cycle */
+    int32_t n_rep;       /* orbit representatives */
+    int64_t ball_total;  /* sum of the representatives' Tanner-ball sizes */
+    int64_t device_bytes;
+} tsx_code_info;
+
+/* Validates `desc`, builds the device-resident tables (edge layout, Tanner
+ * balls of the representatives: the variable layers of the depth-3
+ * unrolled tree of Sec. III / Fig. 3) and computes the girth.  Blocks until
+ * the tables are resident.  Errors: TSX_EINVAL (shift outside
+ * {-1..Z-1}, index outside [0,n), duplicate edge, empty code),
+ * TSX_EUNSUPPORTED (degree, n_b or n above the limits), TSX_ENOMEM,
+ * TSX_ECUDA. */
+TSX_API int load_code(const tsx_code_desc *desc, void *stream, tsx_code **out);
+TSX_API void free_code(tsx_code *code);
+TSX_API int code_info(const tsx_code *code, tsx_code_info *info);
+
+/* ---- trapping-set enumeration (Sec. III) ----------------------------- */
+typedef struct tsx_ts_list tsx_ts_list;
+
+enum {
+    TSX_DEC_NMS_I16 = 0, /* fixed-point normalized min-sum, int16 messages */
+    TSX_DEC_NMS_I8 = 1,  /* the same decoder with int8 check-to-variable storage (sat <= 169) */
+    TSX_DEC_SPA_F32 = 2  /* single-precision sum-product */
+};
+
+typedef struct {
+    int32_t decoder;     /* TSX_DEC_* */
+    int32_t K;           /* maximum iterations (flooding schedule) */
+    int32_t base_llr;    /* channel LLR of every bit, fixed point, units of 1/8 (> 0) */
+    int32_t sat;         /* min-sum message and channel saturation (511 for int16) */
+    int32_t alpha_num;   /* min-sum normalization (alpha_num * m) >> alpha_shift */
+    int32_t alpha_shift;
+    int32_t amp_steps;   /* s: amplitude range [0, 2^s - 1] (min-sum) or s halvings of [0,1] (sum-product) */
+    float spa_clip;      /* sum-product channel/message clip (30) */
+    float spa_amax;      /* sum-product impulse amplitude at eps = 1, LLR units (64) */
+    int32_t max_size;    /* candidate sets: 1..4 nodes from a representative's Tanner ball */
+    int32_t cycle_len;   /* 0, or 2l in 6..8: add the VN sets of 2l-cycles through the
+                            representatives when l > max_size */
+    int32_t record_candidates; /* 1: keep per-candidate records */
+    int64_t cand_begin;  /* decode candidates [cand_begin, cand_end) of the canonical list */
+    int64_t cand_end;    /* -1 = to the end */
+    int32_t warps_per_cta; /* 0 = autotuned */
+    int32_t ctas_per_sm;   /* 0 = autotuned */
+} tsx_enum_params;
+
+/* Fills `p` with the defaults: NMS int16, K=20, base 16, sat 511, alpha 3/4,
+ * s=10, clip 30, amax 64, max_size 3, no cycle sets, records on, all
+ * candidates, autotuned tile. */
+TSX_API void enum_params_default(tsx_enum_params *p);
+
+/* Runs the whole hot path for `code` on `stream`: candidate generation and
+ * canonical dedupe, the impulse decodes with amplitude bisection, extraction
+ * of S1 = Tree(X) or S2 = Tree(TS(X)) with X = supp(x*) u I, (a,b)
+ * classification, canonical form and hash dedupe of the trapping sets.
+ * Asynchronous: returns once the work is enqueued; the results stay in
+ * device memory until ts_list_view() (which synchronizes) copies them out.
+ * Errors: TSX_EINVAL (parameters), TSX_EUNSUPPORTED (decoder/degree
+ * combination), TSX_ENOMEM, TSX_ECUDA.  Device-side overflows and timed-out
+ * waits are reported by ts_list_view(). */
+TSX_API int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void *stream,
+                 tsx_ts_list **out);
+
+typedef struct {
+    int64_t n_cand;        /* candidates decoded */
+    int64_t n_cand_total;  /* canonical candidates of the code and rule */
+    int64_t n_ts;          /* distinct trapping sets */
+    int64_t decodes;
+    int64_t iterations;    /* sum over decodes of the iterations executed */
+    int64_t edge_updates;  /* sum over decodes of E * iterations executed */
+    int64_t acyclic;       /* failing candidates with S1 = S2 = empty */
+    double ms_total;       /* device time of the whole pipeline (CUDA events on the stream) */
+    double ms_candidates;  /* candidate generation */
+    double ms_decode;      /* the impulse-decoding kernel */
+} tsx_enum_stats;
+
+/* Host views of the results, sorted by (a, b, key); valid until
+ * free_ts_list().  Per trapping set i: a[i], b[i]; orbit[i] = Z / |stabilizer|
+ * (1 for CSR codes); count[i] = candidates that produced it; thr[i] /
+ * thr_f[i] = smallest threshold amplitude among them (min-sum integer A /
+ * sum-product eps; the other is -1); flags[i] bit 0 = elementary (every
+ * check touches it at most twice), bits 1-2 = sieve (1: Tree(X), 2:
+ * Tree(TS(X))); key: vars[var_off[i] .. var_off[i] + a[i]) ascending
+ * (the lexicographically smallest circulant shift).
+ * Per candidate c (if records were kept): cand_vars[4c..4c+3] canonical
+ * impulse set (-1 padded); cand_thr[c] / cand_thr_f[c] threshold or -1;
+ * cand_ts[c] index into the sorted list or -1; cand_flags[c] bits 0-1 =
+ * sieve (0 = no failure or acyclic), bit 2 = acyclic failure, bit 3 =
+ * key-pool overflow; cand_decodes[c], cand_iters[c] = decodes run and
+ * iterations executed over them. */
+typedef struct {
+    tsx_enum_stats stats;
+    int64_t n_ts;
+    const int32_t *a, *b, *orbit, *count, *thr, *flags;
+    const float *thr_f;
+    const int64_t *var_off;
+    const int32_t *vars;
+    int64_t n_cand;
+    const int32_t *cand_vars, *cand_thr, *cand_ts, *cand_flags, *cand_decodes, *cand_iters;
+    const float *cand_thr_f;
+} tsx_ts_view;
+
+/* Synchronizes the list's stream, copies the results to host memory (once)
+ * and fills `view`.  Errors: TSX_ENOMEM (the device key pool or hash table
+ * overflowed), TSX_ETIMEDOUT (a device-side wait gave up), TSX_ECUDA. */
+TSX_API int ts_list_view(tsx_ts_list *list, tsx_ts_view *view);
+
+/* Device-side counters only (decodes, iterations, edge updates, number of
+ * trapping sets): synchronizes and copies a few words. */
+TSX_API int ts_list_stats(tsx_ts_list *list, tsx_enum_stats *stats);
+
+TSX_API void free_ts_list(tsx_ts_list *list);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSX_H */

@@ -1,0 +1,23 @@
+"""GB300-native trapping-set enumeration for QC-LDPC codes.
+
+The hot path of the modified Cole importance-sampling method (arXiv
+2208.05795, Sec. III) as a CUDA library for sm_103a with a C ABI
+(include/tsx.h); this package is its thin Python binding.
+"""
+from ._tsx import (  # noqa: F401
+    DECODERS,
+    Code,
+    TsList,
+    TsxError,
+    code_info,
+    enum_params_default,
+    enumerate_ts,
+    free_code,
+    free_ts_list,
+    lib,
+    load_code,
+    make_params,
+    strerror,
+    ts_list_stats,
+    ts_list_view,
+)

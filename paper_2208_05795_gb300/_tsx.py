@@ -1,0 +1,261 @@
+"""ctypes binding of libtsx.so (include/tsx.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts Python
+and numpy arguments into the C structs, calls the entry points of the same
+names, and copies result views into numpy arrays.  If the library is
+missing or cannot be loaded, the calls raise -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtsx.so")
+
+TSX_OK, TSX_EINVAL, TSX_ENOMEM, TSX_ECUDA, TSX_ETIMEDOUT = 0, -1, -2, -3, -4
+TSX_EBUSY, TSX_EUNSUPPORTED, TSX_ENOTFOUND, TSX_EAGAIN = -5, -6, -7, -8
+TSX_CODE_QC, TSX_CODE_CSR = 0, 1
+TSX_DEC_NMS_I16, TSX_DEC_NMS_I8, TSX_DEC_SPA_F32 = 0, 1, 2
+DECODERS = {"nms16": TSX_DEC_NMS_I16, "nms8": TSX_DEC_NMS_I8, "spa": TSX_DEC_SPA_F32}
+
+I32 = C.POINTER(C.c_int32)
+I64 = C.POINTER(C.c_int64)
+F32 = C.POINTER(C.c_float)
+
+
+class TsxError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+        self.status = status
+
+
+class CodeDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("m_b", C.c_int32), ("n_b", C.c_int32), ("Z", C.c_int32),
+                ("shifts", I32), ("n", C.c_int32), ("m", C.c_int32), ("row_ptr", I32), ("col_idx", I32)]
+
+
+class CodeInfo(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32), ("E", C.c_int32),
+                ("Z", C.c_int32), ("n_b", C.c_int32), ("m_b", C.c_int32), ("dv_max", C.c_int32),
+                ("dc_max", C.c_int32), ("girth", C.c_int32), ("n_rep", C.c_int32),
+                ("ball_total", C.c_int64), ("device_bytes", C.c_int64)]
+
+
+class EnumParams(C.Structure):
+    _fields_ = [("decoder", C.c_int32), ("K", C.c_int32), ("base_llr", C.c_int32), ("sat", C.c_int32),
+                ("alpha_num", C.c_int32), ("alpha_shift", C.c_int32), ("amp_steps", C.c_int32),
+                ("spa_clip", C.c_float), ("spa_amax", C.c_float), ("max_size", C.c_int32),
+                ("cycle_len", C.c_int32), ("record_candidates", C.c_int32), ("cand_begin", C.c_int64),
+                ("cand_end", C.c_int64), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
+
+
+class EnumStats(C.Structure):
+    _fields_ = [("n_cand", C.c_int64), ("n_cand_total", C.c_int64), ("n_ts", C.c_int64),
+                ("decodes", C.c_int64), ("iterations", C.c_int64), ("edge_updates", C.c_int64),
+                ("acyclic", C.c_int64), ("ms_total", C.c_double), ("ms_candidates", C.c_double),
+                ("ms_decode", C.c_double)]
+
+
+class TsView(C.Structure):
+    _fields_ = [("stats", EnumStats), ("n_ts", C.c_int64), ("a", I32), ("b", I32), ("orbit", I32),
+                ("count", I32), ("thr", I32), ("flags", I32), ("thr_f", F32), ("var_off", I64),
+                ("vars", I32), ("n_cand", C.c_int64), ("cand_vars", I32), ("cand_thr", I32),
+                ("cand_ts", I32), ("cand_flags", I32), ("cand_decodes", I32), ("cand_iters", I32),
+                ("cand_thr_f", F32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libtsx.so (build it first with paper_2208_05795_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libtsx.so not built ({LIB_PATH}); run paper_2208_05795_gb300.build.build()")
+            L = C.CDLL(LIB_PATH)
+            vp = C.c_void_p
+            L.tsx_strerror.restype = C.c_char_p
+            L.tsx_strerror.argtypes = [C.c_int]
+            L.load_code.argtypes = [C.POINTER(CodeDesc), vp, C.POINTER(vp)]
+            L.load_code.restype = C.c_int
+            L.free_code.argtypes = [vp]
+            L.free_code.restype = None
+            L.code_info.argtypes = [vp, C.POINTER(CodeInfo)]
+            L.code_info.restype = C.c_int
+            L.enum_params_default.argtypes = [C.POINTER(EnumParams)]
+            L.enum_params_default.restype = None
+            L.enumerate_ts.argtypes = [vp, C.POINTER(EnumParams), vp, C.POINTER(vp)]
+            L.enumerate_ts.restype = C.c_int
+            L.ts_list_view.argtypes = [vp, C.POINTER(TsView)]
+            L.ts_list_view.restype = C.c_int
+            L.ts_list_stats.argtypes = [vp, C.POINTER(EnumStats)]
+            L.ts_list_stats.restype = C.c_int
+            L.free_ts_list.argtypes = [vp]
+            L.free_ts_list.restype = None
+            _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().tsx_strerror(int(status)).decode()
+
+
+def _check(status: int, what: str):
+    if status != TSX_OK:
+        raise TsxError(status, what)
+
+
+def _stream_handle(stream):
+    """A cudaStream_t as an integer: an int, a torch stream, or None (the
+    current torch stream when torch has CUDA, else the legacy default)."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+# ---------------------------------------------------------------------------
+# the entry points, same names as the C ABI
+# ---------------------------------------------------------------------------
+class Code:
+    """A loaded code (device-resident tables); frees itself on deletion."""
+
+    def __init__(self, handle, info: CodeInfo):
+        self.h = handle
+        self.info = {k: getattr(info, k) for k, _ in CodeInfo._fields_}
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().free_code(self.h)
+            self.h = None
+
+
+def load_code(code, stream=None) -> Code:
+    """load_code(): `code` has the fields of synth.Code (kind, Z, shifts, n,
+    m, row_ptr, col_idx)."""
+    d = CodeDesc()
+    keep = []
+    if code.kind == "qc":
+        s = _i32(code.shifts)
+        keep.append(s)
+        d.kind, d.m_b, d.n_b, d.Z = TSX_CODE_QC, s.shape[0], s.shape[1], int(code.Z)
+        d.shifts = s.ctypes.data_as(I32)
+    else:
+        rp, ci = _i32(code.row_ptr), _i32(code.col_idx)
+        keep += [rp, ci]
+        d.kind, d.n, d.m = TSX_CODE_CSR, int(code.n), int(code.m)
+        d.row_ptr, d.col_idx = rp.ctypes.data_as(I32), ci.ctypes.data_as(I32)
+    h = C.c_void_p()
+    _check(lib().load_code(C.byref(d), _stream_handle(stream), C.byref(h)), "load_code")
+    info = CodeInfo()
+    _check(lib().code_info(h, C.byref(info)), "code_info")
+    return Code(h, info)
+
+
+def free_code(code: Code):
+    if code.h:
+        lib().free_code(code.h)
+        code.h = None
+
+
+def code_info(code: Code) -> dict:
+    return dict(code.info)
+
+
+def enum_params_default() -> EnumParams:
+    p = EnumParams()
+    lib().enum_params_default(C.byref(p))
+    return p
+
+
+def make_params(**kw) -> EnumParams:
+    p = enum_params_default()
+    for k, v in kw.items():
+        if k == "decoder" and isinstance(v, str):
+            v = DECODERS[v]
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class TsList:
+    """Results of one enumerate_ts call (device-resident until viewed)."""
+
+    def __init__(self, handle, code: Code):
+        self.h = handle
+        self.code = code  # keeps the code alive
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().free_ts_list(self.h)
+            self.h = None
+
+
+def enumerate_ts(code: Code, params=None, stream=None, **kw) -> TsList:
+    p = params if isinstance(params, EnumParams) else make_params(**(params or {}), **kw)
+    h = C.c_void_p()
+    _check(lib().enumerate_ts(code.h, C.byref(p), _stream_handle(stream), C.byref(h)), "enumerate_ts")
+    return TsList(h, code)
+
+
+def _arr(ptr, n, dtype):
+    if n == 0:
+        return np.zeros(0, dtype=dtype)
+    return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
+
+
+def ts_list_view(lst: TsList, check: bool = True) -> dict:
+    """Synchronizes, copies the results out; returns numpy arrays:
+    per TS: a, b, orbit, count, thr, thr_f, flags, keys (list of tuples);
+    per candidate: cand_vars [N,4], cand_thr, cand_thr_f, cand_ts,
+    cand_flags, cand_decodes, cand_iters; and stats."""
+    v = TsView()
+    st = lib().ts_list_view(lst.h, C.byref(v))
+    if check:
+        _check(st, "ts_list_view")
+    nts, nc = int(v.n_ts), int(v.n_cand)
+    out = {"status": st, "stats": {k: getattr(v.stats, k) for k, _ in EnumStats._fields_}}
+    for k in ("a", "b", "orbit", "count", "thr", "flags"):
+        out[k] = _arr(getattr(v, k), nts, np.int32)
+    out["thr_f"] = _arr(v.thr_f, nts, np.float32)
+    off = _arr(v.var_off, nts + 1, np.int64) if nts else np.zeros(1, np.int64)
+    vars_ = _arr(v.vars, int(off[-1]), np.int32)
+    out["keys"] = [tuple(int(x) for x in vars_[off[i]:off[i + 1]]) for i in range(nts)]
+    out["cand_vars"] = _arr(v.cand_vars, 4 * nc, np.int32).reshape(nc, 4)
+    for k in ("cand_thr", "cand_ts", "cand_flags", "cand_decodes", "cand_iters"):
+        out[k] = _arr(getattr(v, k), nc, np.int32)
+    out["cand_thr_f"] = _arr(v.cand_thr_f, nc, np.float32)
+    return out
+
+
+def ts_list_stats(lst: TsList, check: bool = True) -> dict:
+    s = EnumStats()
+    st = lib().ts_list_stats(lst.h, C.byref(s))
+    if check:
+        _check(st, "ts_list_stats")
+    return {k: getattr(s, k) for k, _ in EnumStats._fields_}
+
+
+def free_ts_list(lst: TsList):
+    if lst.h:
+        lib().free_ts_list(lst.h)
+        lst.h = None
