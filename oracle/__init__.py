@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import platform
 import subprocess
 import threading
 from dataclasses import dataclass
@@ -32,11 +33,18 @@ def build(force: bool = False) -> str:
     """Compile oracle.c with gcc (no FMA contraction, so float results match
     the source's operation order on every host)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    stamp = os.path.join(_BUILD, "machine.txt")
+    try:
+        same = open(stamp).read().strip() == platform.machine()
+    except OSError:
+        same = False
+    if force or not same or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
                                "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as f:
+            f.write(platform.machine())
     return _LIB
 
 

@@ -7,6 +7,7 @@ PyTorch extension machinery: the library's ABI is plain C (include/tsx.h).
 from __future__ import annotations
 
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -37,9 +38,19 @@ def _deps_mtime() -> float:
     return max(os.path.getmtime(f) for f in files)
 
 
+STAMP = os.path.join(BUILD, "machine.txt")
+
+
+def _stamp_ok() -> bool:
+    try:
+        return open(STAMP).read().strip() == platform.machine()
+    except OSError:
+        return False
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
+    if not force and os.path.exists(LIB) and _stamp_ok() and os.path.getmtime(LIB) >= _deps_mtime():
         return LIB
     cc = nvcc()
 
@@ -61,6 +72,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(platform.machine())
     return LIB
 
 

@@ -10,6 +10,7 @@ from .codes import (  # noqa: F401
     qc_code,
     csr_code,
     draw_qc,
+    draw_qc_columns,
     peg,
     batch_codes,
     serving_codes,

@@ -155,6 +155,48 @@ def qc_girth_at_least(shifts: np.ndarray, Z: int, g: int) -> bool:
 # generators
 # --------------------------------------------------------------------------
 
+def _closes_4cycle(E: np.ndarray, j: int, Z: int) -> bool:
+    """Does column j close a 4-cycle with an earlier column?  Columns j, j'
+    and rows i1, i2 (all blocks non-zero) form a 4-cycle iff the walk
+    (i1,j) -> (i1,j') -> (i2,j') -> (i2,j) returns to its start modulo Z."""
+    rows = np.flatnonzero(E[:, j] >= 0)
+    for a in range(len(rows)):
+        for b in range(a + 1, len(rows)):
+            i1, i2 = rows[a], rows[b]
+            prev = np.flatnonzero((E[i1, :j] >= 0) & (E[i2, :j] >= 0))
+            if prev.size == 0:
+                continue
+            d = (E[i1, j] - E[i1, prev] + E[i2, prev] - E[i2, j]) % Z
+            if (d == 0).any():
+                return True
+    return False
+
+
+def draw_qc_columns(rng: np.random.Generator, m_b: int, n_b: int, Z: int, girth_min: int,
+                    mask: Optional[np.ndarray] = None, max_tries: int = 20000, name: str = "") -> Code:
+    """Column-greedy draw for larger bases: column j's shifts are drawn
+    uniformly over [0, Z) and redrawn until the column closes no 4-cycle
+    with columns 0..j-1; the finished matrix is accepted only if its girth
+    (breadth-first search) is >= girth_min, else drawn again."""
+    msk = np.ones((m_b, n_b), dtype=bool) if mask is None else np.asarray(mask, dtype=bool)
+    for attempt in range(1, 101):
+        E = np.full((m_b, n_b), -1, dtype=np.int64)
+        ok = True
+        for j in range(n_b):
+            for _ in range(max_tries):
+                E[:, j] = np.where(msk[:, j], rng.integers(0, Z, m_b), -1)
+                if girth_min <= 4 or not _closes_4cycle(E, j, Z):
+                    break
+            else:
+                ok = False
+                break
+        if ok and qc_girth_at_least(E.astype(np.int32), Z, girth_min):
+            code = qc_code(E.astype(np.int32), Z, name=name)
+            code.meta.update(attempts=attempt, girth_min=girth_min)
+            return code
+    raise RuntimeError(f"no {m_b}x{n_b} Z={Z} draw with girth >= {girth_min}")
+
+
 def draw_qc(seed: int, m_b: int, n_b: int, Z: int, girth_min: int,
             mask: Optional[np.ndarray] = None, max_draws: int = 10000,
             rng: Optional[np.random.Generator] = None, name: str = "") -> Code:
@@ -240,24 +282,28 @@ _BATCH_Z = (32, 64, 128, 256, 384)
 def batch_codes(seeds=range(100, 132)) -> list[Code]:
     """Codes of the batching workload: 4 x n_b bases, n_b in [16, 32].
 
-    Per seed: ``rng = default_rng(seed)``; n_b = rng.integers(16, 33);
-    Z = rng.choice((32, 64, 128, 256, 384)); each column has weight 4 or 3
-    with equal probability, a weight-3 column gets its zero block in a row
-    drawn uniformly; then shifts are drawn as in ``draw_qc`` with the same
-    generator until girth >= 6.
+    Per seed: ``rng = default_rng(seed)``; n_b = rng.integers(16, 33); Z is
+    drawn uniformly from those of (32, 64, 128, 256, 384) with Z >= 2 n_b
+    (with 4 rows a girth-6 code needs distinct shift differences per row
+    pair, so n_b <= Z at least); each column has weight 4 or 3 with equal
+    probability, a weight-3 column gets its zero block in a row drawn
+    uniformly; then ``draw_qc_columns`` with the same generator, girth >= 6.
     """
     out = []
     for seed in seeds:
         rng = np.random.default_rng(seed)
         n_b = int(rng.integers(16, 33))
-        Z = int(rng.choice(_BATCH_Z))
+        zs = [z for z in _BATCH_Z if z >= 2 * n_b]
+        Z = int(zs[int(rng.integers(0, len(zs)))])
         mask = np.ones((4, n_b), dtype=bool)
         w3 = rng.integers(0, 2, n_b).astype(bool)
         rows = rng.integers(0, 4, n_b)
         for j in range(n_b):
             if w3[j]:
                 mask[rows[j], j] = False
-        out.append(draw_qc(seed, 4, n_b, Z, 6, mask=mask, rng=rng, name=f"batch{seed}"))
+        code = draw_qc_columns(rng, 4, n_b, Z, 6, mask=mask, name=f"batch{seed}")
+        code.meta.update(seed=seed)
+        out.append(code)
     return out
 
 
@@ -266,8 +312,8 @@ def serving_codes(seed: int, count: int) -> list[Code]:
 
     Per code i: ``rng = default_rng((seed, i))``; m_b in {3, 4}; n_b in
     [2 m_b, 24]; Z drawn from powers of two and their 1.5x multiples in
-    [16, 512] with n_b * Z <= 10,000; full base (all blocks non-zero);
-    shifts drawn until girth >= 6.
+    [16, 512] with 2 n_b <= Z and n_b * Z <= 10,000; full base (all blocks
+    non-zero); ``draw_qc_columns``, girth >= 6.
     """
     zs = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
     out = []
@@ -275,9 +321,9 @@ def serving_codes(seed: int, count: int) -> list[Code]:
         rng = np.random.default_rng((seed, i))
         m_b = int(rng.integers(3, 5))
         n_b = int(rng.integers(2 * m_b, 25))
-        ok = [z for z in zs if n_b * z <= 10000]
+        ok = [z for z in zs if n_b * z <= 10000 and z >= 2 * n_b]
         Z = int(ok[int(rng.integers(0, len(ok)))])
-        out.append(draw_qc(0, m_b, n_b, Z, 6, rng=rng, name=f"serve{seed}_{i}"))
+        out.append(draw_qc_columns(rng, m_b, n_b, Z, 6, name=f"serve{seed}_{i}"))
     return out
 
 

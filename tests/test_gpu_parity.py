@@ -158,12 +158,12 @@ def test_code1_table5_small_sets():
 
 
 def test_batch_code_with_zero_blocks():
+    # a 4 x 25 base with weight-3 and weight-4 columns, Z = 128
     code = synth.batch_codes([103])[0]
-    g = oracle.Graph(code)
-    p = dict(K=15, base_llr=16, amp_steps=8, max_size=2)
-    res = g.enumerate(**p)
-    v = run_lib(code, **p)
-    _full_compare(v, res)
+    w = dict(code=code, K=15, base_llr=16, amp_steps=8, max_size=2, cycle_len=0)
+    v = run_lib(code, **_params(w))
+    g = _sampled_compare(w, v, 80, seed=11)
+    _ts_invariants(g, v, qc=True)
 
 
 # ---------------------------------------------------------------------------
