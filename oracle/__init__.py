@@ -105,8 +105,22 @@ def lib():
             L.og_res_ts.argtypes = [vp, C.c_int, I32P, C.POINTER(C.c_float), I32P]
             L.og_res_ts.restype = C.c_int
             L.og_res_free.argtypes = [vp]
+            L.og_tanhf.argtypes = [C.c_float]
+            L.og_tanhf.restype = C.c_float
+            L.og_atanhf.argtypes = [C.c_float]
+            L.og_atanhf.restype = C.c_float
             _lib = L
     return _lib
+
+
+def tanhf(x: float) -> float:
+    """The sum-product decoder's single-precision tanh (series, IEEE ops)."""
+    return float(lib().og_tanhf(float(x)))
+
+
+def atanhf(x: float) -> float:
+    """The sum-product decoder's single-precision atanh (series, IEEE ops)."""
+    return float(lib().og_atanhf(float(x)))
 
 
 @dataclass

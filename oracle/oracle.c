@@ -411,8 +411,85 @@ int og_decode_nms(const og_graph *g, const int *L, int K, int sat, int an, int a
     return fail;
 }
 
+/* Single-precision tanh and atanh used by the sum-product decoder, from
+ * their series with every operation an IEEE single-precision add, multiply
+ * or divide (no fused multiply-add; ldexpf/frexpf/rintf are exact), so that
+ * any implementation taking the same steps gets the same bits:
+ *   expm1(x), x >= 0: k = rint(x / ln2), r = (x - k ln2_hi) - k ln2_lo
+ *     (Cody-Waite reduction), expm1(r) = r + r^2/2! + ... + r^9/9! by
+ *     Horner, expm1(x) = 2^k (expm1(r) + 1) - 1 for k != 0;
+ *   tanh(y) = sgn(y) e/(e + 2), e = expm1(2|y|);
+ *   atanh(p) = sgn(p) (a + a^3/3 + ... + a^17/17) for a = |p| < 1/4,
+ *     else sgn(p) log(t)/2 with t = (1 + a)/(1 - a), t = m 2^e, m in
+ *     [sqrt(1/2), sqrt(2)), log t = e ln2 + 2 (s + s^3/3 + ... + s^13/13),
+ *     s = (m - 1)/(m + 1). */
+static const float OG_LN2_HI = 0.693145751953125f;
+static const float OG_LN2_LO = 1.42860676533018704e-06f;
+static const float OG_INV_LN2 = 1.44269504088896341f;
+static const float OG_LN2 = 0.693147180559945309f;
+static const float OG_SQRT_HALF = 0.707106781186547524f;
+
+static float og_expm1_pos(float x) {
+    float k = rintf(x * OG_INV_LN2);
+    float r = (x - k * OG_LN2_HI) - k * OG_LN2_LO;
+    float p = 1.0f / 362880.0f;
+    p = p * r + 1.0f / 40320.0f;
+    p = p * r + 1.0f / 5040.0f;
+    p = p * r + 1.0f / 720.0f;
+    p = p * r + 1.0f / 120.0f;
+    p = p * r + 1.0f / 24.0f;
+    p = p * r + 1.0f / 6.0f;
+    p = p * r + 0.5f;
+    p = p * r + 1.0f;
+    p = p * r;
+    if (k == 0.0f) return p;
+    return ldexpf(p + 1.0f, (int)k) - 1.0f;
+}
+
+float og_tanhf(float y) {
+    float a = fabsf(y);
+    float e = og_expm1_pos(a + a);
+    float t = e / (e + 2.0f);
+    return y < 0.0f ? -t : t;
+}
+
+float og_atanhf(float p) {
+    float a = fabsf(p), r;
+    if (a < 0.25f) {
+        float a2 = a * a;
+        float q = 1.0f / 17.0f;
+        q = q * a2 + 1.0f / 15.0f;
+        q = q * a2 + 1.0f / 13.0f;
+        q = q * a2 + 1.0f / 11.0f;
+        q = q * a2 + 1.0f / 9.0f;
+        q = q * a2 + 1.0f / 7.0f;
+        q = q * a2 + 1.0f / 5.0f;
+        q = q * a2 + 1.0f / 3.0f;
+        q = q * a2 + 1.0f;
+        r = q * a;
+    } else {
+        float t = (1.0f + a) / (1.0f - a);
+        int e;
+        float m = frexpf(t, &e);
+        if (m < OG_SQRT_HALF) { m = m + m; e = e - 1; }
+        float s = (m - 1.0f) / (m + 1.0f);
+        float s2 = s * s;
+        float q = 1.0f / 13.0f;
+        q = q * s2 + 1.0f / 11.0f;
+        q = q * s2 + 1.0f / 9.0f;
+        q = q * s2 + 1.0f / 7.0f;
+        q = q * s2 + 1.0f / 5.0f;
+        q = q * s2 + 1.0f / 3.0f;
+        q = q * s2 + 1.0f;
+        float lg = (float)e * OG_LN2 + (s + s) * q;
+        r = 0.5f * lg;
+    }
+    return p < 0.0f ? -r : r;
+}
+
 /* Floating-point sum-product (same flooding schedule and stopping rule).
  *   check:  r(c->v) = 2 atanh( prod over v' != v, ascending, of tanh(q(v'->c)/2) ),
+ *           with og_tanhf / og_atanhf above,
  *           +-clip when |prod| >= 1, then clipped to [-clip, clip]
  *   var:    P_v = L_v + r(c_0->v) + r(c_1->v) + ... (checks ascending);
  *           q(v->c) = clip(P_v - r(c->v)); x_v = [P_v < 0]
@@ -433,13 +510,13 @@ int og_decode_spa(const og_graph *g, const float *L, int K, float clip, int wsta
     for (int k = 1; k <= K && u != 0; k++) {
         for (int c = 0; c < g->m; c++) {
             int d = g->cdeg[c];
-            for (int p = 0; p < d; p++) t[p] = tanhf(q[c * g->dcmax + p] * 0.5f);
+            for (int p = 0; p < d; p++) t[p] = og_tanhf(q[c * g->dcmax + p] * 0.5f);
             for (int p = 0; p < d; p++) {
                 float prod = 1.0f;
                 for (int p2 = 0; p2 < d; p2++) if (p2 != p) prod = prod * t[p2];
                 float rr;
                 if (fabsf(prod) >= 1.0f) rr = prod > 0.0f ? clip : -clip;
-                else rr = 2.0f * atanhf(prod);
+                else rr = 2.0f * og_atanhf(prod);
                 r[c * g->dcmax + p] = clampf(rr, -clip, clip);
             }
         }
@@ -481,13 +558,13 @@ void og_spa_posterior(const og_graph *g, const float *L, int K, float clip, floa
     for (int k = 1; k <= K; k++) {
         for (int c = 0; c < g->m; c++) {
             int d = g->cdeg[c];
-            for (int p = 0; p < d; p++) t[p] = tanhf(q[c * g->dcmax + p] * 0.5f);
+            for (int p = 0; p < d; p++) t[p] = og_tanhf(q[c * g->dcmax + p] * 0.5f);
             for (int p = 0; p < d; p++) {
                 float prod = 1.0f;
                 for (int p2 = 0; p2 < d; p2++) if (p2 != p) prod = prod * t[p2];
                 float rr;
                 if (fabsf(prod) >= 1.0f) rr = prod > 0.0f ? clip : -clip;
-                else rr = 2.0f * atanhf(prod);
+                else rr = 2.0f * og_atanhf(prod);
                 r[c * g->dcmax + p] = clampf(rr, -clip, clip);
             }
         }

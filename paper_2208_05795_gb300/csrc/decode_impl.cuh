@@ -159,6 +159,86 @@ struct Grp {
     }
 };
 
+// ---------------------------------------------------------------------------
+// single-precision tanh / atanh of the sum-product check update, from their
+// series with IEEE-rounded adds, multiplies and divides only (no fused
+// multiply-add), so the result is the same on every conforming machine:
+//   expm1(x), x >= 0: k = rint(x/ln2), r = (x - k ln2_hi) - k ln2_lo
+//     (Cody-Waite reduction), expm1(r) = sum_{i=1..9} r^i/i! by Horner,
+//     expm1(x) = 2^k (expm1(r) + 1) - 1 if k != 0;
+//   tanh(y) = sgn(y) e / (e + 2), e = expm1(2|y|);
+//   atanh(p) = sgn(p) sum_{j=0..8} a^(2j+1)/(2j+1) for a = |p| < 1/4, else
+//     sgn(p) log(t)/2, t = (1+a)/(1-a) = m 2^e with m in [sqrt(1/2),
+//     sqrt(2)), log t = e ln2 + 2 sum_{j=0..6} s^(2j+1)/(2j+1),
+//     s = (m-1)/(m+1).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float hadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float hsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float hmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float hdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+__device__ __forceinline__ float spa_expm1_pos(float x) {
+    const float k = rintf(hmul(x, 0x1.715476p+0f));
+    const float r = hsub(hsub(x, hmul(k, 0x1.62e4p-1f)), hmul(k, 0x1.7f7d1cp-20f));
+    float p = 0x1.71de3ap-19f;  // 1/9!
+    p = hadd(hmul(p, r), 0x1.a01a02p-16f);
+    p = hadd(hmul(p, r), 0x1.a01a02p-13f);
+    p = hadd(hmul(p, r), 0x1.6c16c2p-10f);
+    p = hadd(hmul(p, r), 0x1.111112p-7f);
+    p = hadd(hmul(p, r), 0x1.555556p-5f);
+    p = hadd(hmul(p, r), 0x1.555556p-3f);
+    p = hadd(hmul(p, r), 0.5f);
+    p = hadd(hmul(p, r), 1.0f);
+    p = hmul(p, r);
+    if (k == 0.0f) return p;
+    return hsub(ldexpf(hadd(p, 1.0f), (int)k), 1.0f);
+}
+
+__device__ __forceinline__ float spa_tanhf(float y) {
+    const float a = fabsf(y);
+    const float e = spa_expm1_pos(hadd(a, a));
+    const float t = hdiv(e, hadd(e, 2.0f));
+    return y < 0.0f ? -t : t;
+}
+
+__device__ __forceinline__ float spa_atanhf(float p) {
+    const float a = fabsf(p);
+    float r;
+    if (a < 0.25f) {
+        const float a2 = hmul(a, a);
+        float q = 0x1.e1e1e2p-5f;  // 1/17
+        q = hadd(hmul(q, a2), 0x1.111112p-4f);
+        q = hadd(hmul(q, a2), 0x1.3b13b2p-4f);
+        q = hadd(hmul(q, a2), 0x1.745d18p-4f);
+        q = hadd(hmul(q, a2), 0x1.c71c72p-4f);
+        q = hadd(hmul(q, a2), 0x1.24924ap-3f);
+        q = hadd(hmul(q, a2), 0x1.99999ap-3f);
+        q = hadd(hmul(q, a2), 0x1.555556p-2f);
+        q = hadd(hmul(q, a2), 1.0f);
+        r = hmul(q, a);
+    } else {
+        const float t = hdiv(hadd(1.0f, a), hsub(1.0f, a));
+        int e;
+        float m = frexpf(t, &e);
+        if (m < 0x1.6a09e6p-1f) {
+            m = hadd(m, m);
+            e = e - 1;
+        }
+        const float s = hdiv(hsub(m, 1.0f), hadd(m, 1.0f));
+        const float s2 = hmul(s, s);
+        float q = 0x1.3b13b2p-4f;  // 1/13
+        q = hadd(hmul(q, s2), 0x1.745d18p-4f);
+        q = hadd(hmul(q, s2), 0x1.c71c72p-4f);
+        q = hadd(hmul(q, s2), 0x1.24924ap-3f);
+        q = hadd(hmul(q, s2), 0x1.99999ap-3f);
+        q = hadd(hmul(q, s2), 0x1.555556p-2f);
+        q = hadd(hmul(q, s2), 1.0f);
+        const float lg = hadd(hmul((float)e, 0x1.62e43p-1f), hmul(hadd(s, s), q));
+        r = hmul(0.5f, lg);
+    }
+    return p < 0.0f ? -r : r;
+}
+
 // misc area of a slot
 struct Misc {
     int red[16];
@@ -259,7 +339,7 @@ struct Decoder {
                     const float ro = first ? 0.0f : (float)R[e0 + p * estride];
                     par ^= Pv < 0.0f;
                     const float q = clampf_(__fsub_rn(Pv, ro), -clip, clip);
-                    t[p] = tanhf(__fmul_rn(q, 0.5f));
+                    t[p] = spa_tanhf(__fmul_rn(q, 0.5f));
                 }
             }
             if (writeR) {
@@ -272,7 +352,7 @@ struct Decoder {
                             if (p2 < deg && p2 != p) prod = __fmul_rn(prod, t[p2]);
                         float rr;
                         if (fabsf(prod) >= 1.0f) rr = prod > 0.0f ? clip : -clip;
-                        else rr = __fmul_rn(2.0f, atanhf(prod));
+                        else rr = __fmul_rn(2.0f, spa_atanhf(prod));
                         R[e0 + p * estride] = (msg)clampf_(rr, -clip, clip);
                     }
                 }

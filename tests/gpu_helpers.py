@@ -45,13 +45,13 @@ def oracle_records(res):
 
 
 def lib_ts(v):
-    """key -> (a, b, orbit, count, thr, elementary)"""
+    """key -> (a, b, orbit, count, thr, thr_f, elementary)"""
     out = {}
     for i, k in enumerate(v["keys"]):
         out[k] = (int(v["a"][i]), int(v["b"][i]), int(v["orbit"][i]), int(v["count"][i]),
-                  int(v["thr"][i]), bool(v["flags"][i] & 1))
+                  int(v["thr"][i]), float(v["thr_f"][i]), bool(v["flags"][i] & 1))
     return out
 
 
 def oracle_ts(res):
-    return {t.key: (t.a, t.b, t.orbit, t.count, t.thr, t.elementary) for t in res.ts_list}
+    return {t.key: (t.a, t.b, t.orbit, t.count, t.thr, float(t.thr_f), t.elementary) for t in res.ts_list}

@@ -107,7 +107,10 @@ def test_qc96_int8_storage_bit_exact():
     _full_compare(v, res)
 
 
-def test_qc96_spa_within_tolerance():
+def test_qc96_spa_bit_exact():
+    # both sides evaluate tanh/atanh by the same series with IEEE-rounded
+    # operations, so the float decoder agrees bit for bit (well inside the
+    # 1e-3 threshold tolerance)
     w = synth.workload("qc96")
     g = oracle.Graph(w["code"])
     p = _params(w, amp_steps=12)
@@ -115,15 +118,9 @@ def test_qc96_spa_within_tolerance():
     v = run_lib(w["code"], decoder="spa", **p)
     lr, orr = lib_records(v), oracle_records(res)
     assert lr.keys() == orr.keys()
-    band = 0
-    for t, (thr, thr_f, key, sieve, dec, it) in orr.items():
-        lthr_f, lkey = lr[t][1], lr[t][2]
-        assert abs(lthr_f - thr_f) <= 1e-3, (t, lthr_f, thr_f)
-        if lthr_f == thr_f:
-            assert lkey == key, t
-        else:
-            band += 1
-    assert band <= len(orr) // 100
+    for t, rec in orr.items():
+        assert abs(lr[t][1] - rec[1]) <= 1e-3, (t, lr[t], rec)
+    _full_compare(v, res)
 
 
 def test_planted_codeword_and_tree_code():
@@ -222,7 +219,7 @@ def _ts_invariants(g, v, qc):
     ts = v["cand_ts"]
     counts = np.bincount(ts[ts >= 0], minlength=len(v["keys"]))
     assert np.array_equal(counts, v["count"])
-    for i, key in enumerate(v["keys"][:2000]):
+    for i, key in enumerate(v["keys"][:500]):
         cnt = H[:, list(key)].sum(axis=1)
         assert (int(v["a"][i]), int(v["b"][i])) == (len(key), int((cnt % 2).sum()))
         live = cnt >= 2
@@ -267,9 +264,10 @@ def test_peg1008_spa_shard_sampled():
     keys = v["keys"]
     for j, i in enumerate(idx):
         assert abs(float(v["cand_thr_f"][i]) - float(res.thr_f[j])) <= 1e-3
-        if float(v["cand_thr_f"][i]) == float(res.thr_f[j]):
-            ts = int(v["cand_ts"][i])
-            assert (keys[ts] if ts >= 0 else None) == (res.ts_list[res.ts[j]].key if res.ts[j] >= 0 else None)
+        assert float(v["cand_thr_f"][i]) == float(res.thr_f[j])
+        assert int(v["cand_iters"][i]) == int(res.iters[j])
+        ts = int(v["cand_ts"][i])
+        assert (keys[ts] if ts >= 0 else None) == (res.ts_list[res.ts[j]].key if res.ts[j] >= 0 else None)
 
 
 @pytest.fixture(scope="module")

@@ -228,3 +228,18 @@ def test_candidates_brute_force_definition():
     got = set(tuple(int(x) for x in r[1:1 + r[0]]) for r in g.candidates(3, 0))
     assert got == keys
     assert len(got) == 9118
+
+
+def test_series_tanh_atanh_error_bounds():
+    # the decoder's tanh/atanh against double-precision math: a few ulp
+    xs = np.concatenate([np.linspace(-15, 15, 4001), np.geomspace(1e-8, 1, 400), -np.geomspace(1e-8, 1, 400)])
+    for x in xs.astype(np.float32):
+        got, want = oracle.tanhf(x), np.tanh(np.float64(x))
+        assert abs(got - want) <= 4 * np.spacing(np.float32(abs(want)) if want else np.float32(1e-45)) + 1e-45, x
+    ps = np.concatenate([np.linspace(-0.999, 0.999, 4001), np.geomspace(1e-8, 0.9999, 400),
+                         -np.geomspace(1e-8, 0.9999, 400), [0.9999999, -0.9999999]]).astype(np.float32)
+    for p in ps:
+        got, want = oracle.atanhf(p), np.arctanh(np.float64(p))
+        assert abs(got - want) <= 4 * np.spacing(np.float32(abs(want))) + 1e-45, p
+    assert oracle.tanhf(0.0) == 0.0 and oracle.atanhf(0.0) == 0.0
+    assert oracle.tanhf(20.0) == 1.0
