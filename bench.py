@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--decoder", default="nms16", choices=["nms16", "nms8", "spa"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cand-limit", type=int, default=-1,
+                    help="decode only the first N canonical candidates (profiling a bounded case)")
     return ap.parse_args()
 
 
@@ -209,6 +211,8 @@ def run_ours(args):
     params = params_of(w, args.decoder)
     if args.decoder == "nms8":
         params["sat"] = 127
+    if args.cand_limit >= 0:
+        params["cand_end"] = args.cand_limit
     stream = torch.cuda.Stream()
     code = tsx.load_code(w["code"], stream=stream)
     info = code.info
@@ -289,7 +293,7 @@ def run_ours(args):
     avg_dec_ms = sum(ms_dec) / len(ms_dec)
     eu_per_step = eu / args.steps
     achieved = ALG_OPS_PER_EDGE * eu_per_step / (avg_dec_ms / 1e3) / 1e12
-    cpu, _ = cpu_baseline(w, args.decoder, args.cpu_seconds) if world == 1 or rank == 0 else (None, None)
+    cpu = cpu_baseline(w, args.decoder, args.cpu_seconds)[0] if args.cpu_seconds > 0 else None
     line = {
         "metric": "impulse-decode edge-updates/s",
         "value": value,
@@ -303,7 +307,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32" if args.decoder == "spa" else ("int8" if args.decoder == "nms8" else "int16"),
         "data": "synthetic",
-        "config": {"workload": args.workload, "decoder": args.decoder, "n": info["n"], "m": info["m"],
+        "config": {"workload": args.workload + (f"[:{args.cand_limit}]" if args.cand_limit >= 0 else ""),
+                   "decoder": args.decoder, "n": info["n"], "m": info["m"],
                    "E": info["E"], "girth": info["girth"], "K": w["K"], "amp_steps": w["amp_steps"],
                    "base_llr": w["base_llr"], "n_cand": int(s["n_cand"]), "parallelism": f"replicas{world}",
                    "l2": "flushed before each step (256 MB write)"},
