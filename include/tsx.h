@@ -124,8 +124,10 @@ typedef struct {
     int32_t record_candidates; /* 1: keep per-candidate records */
     int64_t cand_begin;  /* decode candidates [cand_begin, cand_end) of the canonical list */
     int64_t cand_end;    /* -1 = to the end */
-    int32_t warps_per_cta; /* 0 = autotuned */
-    int32_t ctas_per_sm;   /* 0 = autotuned */
+    int32_t warps_per_cta; /* warps per codeword group (0 = automatic) */
+    int32_t ctas_per_sm;   /* 0 = as many as are resident */
+    int32_t kernel;        /* min-sum kernel: 0 automatic, 1 one codeword per group,
+                              2 two codewords per lane (16-bit halves) */
 } tsx_enum_params;
 
 /* Fills `p` with the defaults: NMS int16, K=20, base 16, sat 511, alpha 3/4,
@@ -156,6 +158,7 @@ typedef struct {
     double ms_total;       /* device time of the whole pipeline (CUDA events on the stream) */
     double ms_candidates;  /* candidate generation */
     double ms_decode;      /* the impulse-decoding kernel */
+    double ms_sieve;       /* extraction, classification, canonical form and dedupe */
 } tsx_enum_stats;
 
 /* Host views of the results, sorted by (a, b, key); valid until

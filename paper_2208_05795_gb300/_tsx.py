@@ -50,14 +50,15 @@ class EnumParams(C.Structure):
                 ("alpha_num", C.c_int32), ("alpha_shift", C.c_int32), ("amp_steps", C.c_int32),
                 ("spa_clip", C.c_float), ("spa_amax", C.c_float), ("max_size", C.c_int32),
                 ("cycle_len", C.c_int32), ("record_candidates", C.c_int32), ("cand_begin", C.c_int64),
-                ("cand_end", C.c_int64), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32)]
+                ("cand_end", C.c_int64), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("kernel", C.c_int32)]
 
 
 class EnumStats(C.Structure):
     _fields_ = [("n_cand", C.c_int64), ("n_cand_total", C.c_int64), ("n_ts", C.c_int64),
                 ("decodes", C.c_int64), ("iterations", C.c_int64), ("edge_updates", C.c_int64),
                 ("acyclic", C.c_int64), ("ms_total", C.c_double), ("ms_candidates", C.c_double),
-                ("ms_decode", C.c_double)]
+                ("ms_decode", C.c_double), ("ms_sieve", C.c_double)]
 
 
 class TsView(C.Structure):

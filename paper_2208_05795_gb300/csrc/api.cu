@@ -41,7 +41,7 @@ struct tsx_ts_list {
     std::vector<void *> bufs;
     EnumBuffers b{};
     Counters *ctr = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // start, decode start, decode end, end
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, decode, sieve, compact, end
     int *ts_off = nullptr, *ts_count = nullptr, *ts_thr = nullptr, *slot_map = nullptr;
     // host results
     bool oom = false;
@@ -281,6 +281,11 @@ extern "C" int load_code(const tsx_code_desc *desc, void *stream, tsx_code **out
     DevCode &d = c->d;
     d.kind = h.kind; d.n = h.n; d.m = h.m; d.E = h.E; d.Z = h.Z; d.n_b = h.n_b; d.m_b = h.m_b;
     d.dv_max = h.dv_max; d.dc_max = h.dc_max; d.girth = girth;
+    d.dc_min = h.dc_max;
+    for (int c = 0; c < (h.kind == TSX_CODE_QC ? h.m_b : h.m); c++) {
+        const int dc = h.kind == TSX_CODE_QC ? h.rdeg[c] : h.c_ptr[c + 1] - h.c_ptr[c];
+        if (dc < d.dc_min) d.dc_min = dc;
+    }
     d.wstart = std::max(1, girth / 2);
     d.n_rep = n_rep;
     d.rdeg = (const int16_t *)(dev + o_rdeg); d.reoff = (const int32_t *)(dev + o_reoff);
@@ -373,7 +378,8 @@ static int check_params(const tsx_enum_params &p) {
     if (p.cycle_len != 0 && (p.cycle_len < 4 || p.cycle_len > 8 || (p.cycle_len & 1))) return TSX_EINVAL;
     if (p.cand_begin < 0) return TSX_EINVAL;
     if (p.cand_end >= 0 && p.cand_end < p.cand_begin) return TSX_EINVAL;
-    if (p.warps_per_cta < 0 || p.ctas_per_sm < 0) return TSX_EINVAL;
+    if (p.warps_per_cta < 0 || p.warps_per_cta > 16 || p.ctas_per_sm < 0) return TSX_EINVAL;
+    if (p.kernel < 0 || p.kernel > 2) return TSX_EINVAL;
     return TSX_OK;
 }
 
@@ -441,13 +447,7 @@ extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void 
     if (p.cand_end >= 0) n_rec = std::min<long long>(n_rec, p.cand_end - p.cand_begin);
     if (n_rec < 0) n_rec = 0;
 
-    LaunchShape sh;
-    int G = 0, groups = 0;
-    if (p.warps_per_cta > 0) { /* explicit tile: warps per CTA = groups * G with G = 1 */
-        G = 1;
-        groups = p.warps_per_cta;
-    }
-    if (!plan_shape(g, p.decoder, G, groups, p.ctas_per_sm, code->num_sms, &sh)) return TSX_EUNSUPPORTED;
+    if (!decode_fits(g, p.decoder)) return TSX_EUNSUPPORTED;
 
     tsx_ts_list *L = new tsx_ts_list();
     L->code = code;
@@ -473,8 +473,10 @@ extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void 
     b.cands = d_cands;
     b.cand_begin = p.cand_begin;
     b.cand_end = p.cand_end;
-    b.record = p.record_candidates ? 1 : 0;
-    const long long nr = p.record_candidates ? n_rec : 0;
+    b.record = 1;
+    const long long nr = n_rec;  // the sieve reads the records, so they are always kept
+    b.nw = (g.n + 31) / 32;
+    b.xstar = lalloc<uint32_t>(L, (size_t)n_rec * b.nw, s);
     b.c_thr = lalloc<int>(L, nr, s);
     b.c_thr_f = lalloc<float>(L, nr, s);
     b.c_slot = lalloc<int>(L, nr, s);
@@ -541,11 +543,15 @@ extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void 
             return bail(TSX_ECUDA);
     }
     if (cudaEventRecord(L->ev[1], s) != cudaSuccess) return bail(TSX_ECUDA);
-    if (launch_enum(g, dp, b, sh, s) != cudaSuccess) return bail(TSX_ECUDA);
+    if (launch_decode(g, dp, b, p.warps_per_cta, 0, p.ctas_per_sm, code->num_sms, p.kernel == 1 ? 1 : 0, s) !=
+        cudaSuccess)
+        return bail(TSX_ECUDA);
     if (cudaEventRecord(L->ev[2], s) != cudaSuccess) return bail(TSX_ECUDA);
+    if (launch_sieve(g, b, p.decoder, code->num_sms, s) != cudaSuccess) return bail(TSX_ECUDA);
+    if (cudaEventRecord(L->ev[3], s) != cudaSuccess) return bail(TSX_ECUDA);
     if (launch_compact(b, nr, L->ts_off, L->ts_count, L->ts_thr, L->slot_map, s) != cudaSuccess)
         return bail(TSX_ECUDA);
-    if (cudaEventRecord(L->ev[3], s) != cudaSuccess) return bail(TSX_ECUDA);
+    if (cudaEventRecord(L->ev[4], s) != cudaSuccess) return bail(TSX_ECUDA);
     *out = L;
     return TSX_OK;
 }
@@ -567,9 +573,10 @@ static void fill_stats(tsx_ts_list *L, const Counters &c, tsx_enum_stats &s) {
     s.edge_updates = (int64_t)c.edge_updates;
     s.acyclic = (int64_t)c.acyclic;
     float ms = 0.0f;
-    if (L->ev[3] && cudaEventElapsedTime(&ms, L->ev[0], L->ev[3]) == cudaSuccess) s.ms_total = ms;
+    if (L->ev[4] && cudaEventElapsedTime(&ms, L->ev[0], L->ev[4]) == cudaSuccess) s.ms_total = ms;
     if (L->ev[1] && cudaEventElapsedTime(&ms, L->ev[0], L->ev[1]) == cudaSuccess) s.ms_candidates = ms;
     if (L->ev[2] && cudaEventElapsedTime(&ms, L->ev[1], L->ev[2]) == cudaSuccess) s.ms_decode = ms;
+    if (L->ev[3] && cudaEventElapsedTime(&ms, L->ev[2], L->ev[3]) == cudaSuccess) s.ms_sieve = ms;
 }
 
 extern "C" int ts_list_stats(tsx_ts_list *L, tsx_enum_stats *stats) {

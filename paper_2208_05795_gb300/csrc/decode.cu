@@ -1,32 +1,51 @@
-// decode.cu -- host side of the decoding kernel: shared-memory layout,
-// launch shape, dispatch to the per-decoder instantiations, and the
-// compaction of the trapping-set hash table.
+// decode.cu -- host side of the decoding and sieve kernels: shared-memory
+// layouts, launch shapes, dispatch, and the compaction of the trapping-set
+// hash table.
 #include "decode_impl.cuh"
 
 namespace tsx {
 
-cudaError_t launch_enum_i16(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, cudaStream_t);
-cudaError_t launch_enum_i8(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, cudaStream_t);
-cudaError_t launch_enum_spa(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, cudaStream_t);
+// per-decoder translation units
+cudaError_t launch_nms16(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, bool pair,
+                         cudaStream_t);
+cudaError_t launch_nms8(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, bool pair,
+                        cudaStream_t);
+cudaError_t launch_spa(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, cudaStream_t);
+cudaError_t launch_sieve_kernel(const DevCode &, const EnumBuffers &, const LaunchShape &, int is_float,
+                                cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// host side: layout, shape, dispatch
-// ---------------------------------------------------------------------------
-static int msg_bytes(int decoder) { return decoder == TSX_DEC_NMS_I8 ? 1 : (decoder == TSX_DEC_SPA_F32 ? 4 : 2); }
-static int post_bytes(int decoder) { return decoder == TSX_DEC_SPA_F32 ? 4 : 2; }
+namespace {
 
-static SlotLayout make_layout(const DevCode &g, int decoder) {
+enum { kLayScalar = 0, kLayPair = 1, kLaySieve = 2 };
+
+int msg_bytes(int decoder) { return decoder == TSX_DEC_NMS_I8 ? 1 : (decoder == TSX_DEC_SPA_F32 ? 4 : 2); }
+int post_bytes(int decoder) { return decoder == TSX_DEC_SPA_F32 ? 4 : 2; }
+
+SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
     SlotLayout L{};
     L.tables_bytes = al16(tab_offsets(g).total);
-    int rbytes = g.E * msg_bytes(decoder);
-    if (rbytes < 4 * g.m) rbytes = 4 * g.m;
-    if (rbytes < 2 * g.n) rbytes = 2 * g.n;
     const int nw = (g.n + 31) / 32;
     int x = 0;
-    L.r_off = x; x += al16(rbytes);
-    L.p_off = x; x += al16(g.n * post_bytes(decoder));
-    L.xa_off = x; x += al16(nw * 4);
-    L.xb_off = x; x += al16(nw * 4);
+    if (kind == kLayScalar) {
+        L.r_off = x; x += al16(g.E * msg_bytes(decoder));
+        L.p_off = x; x += al16(g.n * post_bytes(decoder));
+        L.xa_off = x; x += al16(nw * 4);
+        L.xb_off = x; x += al16(nw * 4);
+    } else if (kind == kLayPair) {
+        const int rsz = decoder == TSX_DEC_NMS_I8 ? 2 : 4;
+        const int xstride = (nw + 3) & ~3;
+        L.r_off = x; x += al16(g.E * rsz);
+        L.p_off = x; x += al16(g.n * 4);
+        L.xa_off = x; x += al16(4 * xstride * 4);
+        L.xb_off = L.xa_off;
+    } else {
+        int rbytes = 4 * g.m;
+        if (rbytes < 2 * g.n) rbytes = 2 * g.n;
+        L.r_off = x; x += al16(rbytes);
+        L.p_off = x; x += al16(2 * g.n);
+        L.xa_off = x; x += al16(nw * 4);
+        L.xb_off = L.xa_off;
+    }
     L.misc_off = x; x += al16((int)sizeof(Misc));
     L.slot_bytes = x;
     return L;
@@ -34,53 +53,77 @@ static SlotLayout make_layout(const DevCode &g, int decoder) {
 
 constexpr int kSmemCta = 227 * 1024;
 
-bool plan_shape(const DevCode &g, int decoder, int G, int groups, int ctas_per_sm, int num_sms,
-                LaunchShape *out) {
+bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_per_sm, int num_sms,
+          LaunchShape *out) {
     LaunchShape sh{};
-    sh.lay = make_layout(g, decoder);
+    sh.lay = make_layout(g, decoder, kind);
     const int room = kSmemCta - sh.lay.tables_bytes;
     const int fit = room / sh.lay.slot_bytes;
     if (fit < 1) return false;
+    if (kind == kLaySieve) G = 1;
     if (G <= 0) {
         const int want_warps = 24;
         G = (want_warps + fit - 1) / fit;
-        const int work = g.m < g.n ? g.m : g.n;
+        int work = g.m < g.n ? g.m : g.n;
+        if (g.kind == TSX_CODE_QC && g.Z < work) work = g.Z;  // QC passes run block by block
         int gmax = work / 32;
         if (gmax < 1) gmax = 1;
         if (G > gmax) G = gmax;
-        if (G > 16) G = 16;  // one 512-thread CTA per codeword at most
+        if (G > 16) G = 16;
         if (G < 1) G = 1;
     }
     int gmax_cta = 16 / G;  // at most 512 threads per CTA
     if (gmax_cta < 1) gmax_cta = 1;
     if (gmax_cta > fit) gmax_cta = fit;
-    if (gmax_cta < 1) return false;
+    if (G > 1 && gmax_cta > 15) gmax_cta = 15;  // named barriers 1..15
     if (groups <= 0 || groups > gmax_cta) groups = gmax_cta;
     sh.G = G;
     sh.groups = groups;
     sh.smem_bytes = sh.lay.tables_bytes + groups * sh.lay.slot_bytes;
-    int per_sm = ctas_per_sm;
-    if (per_sm <= 0) {
-        const int by_smem = (228 * 1024) / (sh.smem_bytes + 1024);
-        const int by_threads = 2048 / (groups * G * 32);
-        per_sm = by_smem < by_threads ? by_smem : by_threads;
-        if (per_sm > 32) per_sm = 32;
-        if (per_sm < 1) per_sm = 1;
-    }
-    sh.ctas = per_sm * num_sms;
     sh.num_sms = num_sms;
     sh.per_sm_req = ctas_per_sm;
+    sh.ctas = num_sms;
     *out = sh;
     return true;
 }
 
-cudaError_t launch_enum(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b,
-                        const LaunchShape &sh, cudaStream_t st) {
+// the two-codeword kernel keeps every biased quantity inside 16 bits
+bool pair_ok(const DevCode &g, const DecodeParams &dp) {
+    if (dp.decoder == TSX_DEC_SPA_F32) return false;
+    const int B = dp.decoder == TSX_DEC_NMS_I8 ? 128 : 1024;
+    const long long an_sat = (long long)dp.alpha_num * dp.sat;
+    if (an_sat >= 65536) return false;
+    const long long rmax = an_sat >> dp.alpha_shift;
+    if (rmax > (dp.decoder == TSX_DEC_NMS_I8 ? 127 : B)) return false;
+    if ((long long)(g.dv_max + 2) * dp.sat > 0x8000 - B) return false;
+    if ((long long)g.dv_max * B > 0x8000 - dp.sat) return false;
+    return true;
+}
+
+}  // namespace
+
+cudaError_t launch_decode(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, int G, int groups,
+                          int ctas_per_sm, int num_sms, int force_scalar, cudaStream_t st) {
+    const bool pair = !force_scalar && pair_ok(g, dp);
+    LaunchShape sh;
+    if (!plan(g, dp.decoder, pair ? kLayPair : kLayScalar, G, groups, ctas_per_sm, num_sms, &sh))
+        return cudaErrorInvalidConfiguration;
     switch (dp.decoder) {
-        case TSX_DEC_NMS_I16: return launch_enum_i16(g, dp, b, sh, st);
-        case TSX_DEC_NMS_I8: return launch_enum_i8(g, dp, b, sh, st);
-        default: return launch_enum_spa(g, dp, b, sh, st);
+        case TSX_DEC_NMS_I16: return launch_nms16(g, dp, b, sh, pair, st);
+        case TSX_DEC_NMS_I8: return launch_nms8(g, dp, b, sh, pair, st);
+        default: return launch_spa(g, dp, b, sh, st);
     }
+}
+
+cudaError_t launch_sieve(const DevCode &g, const EnumBuffers &b, int decoder, int num_sms, cudaStream_t st) {
+    LaunchShape sh;
+    if (!plan(g, decoder, kLaySieve, 1, 0, 0, num_sms, &sh)) return cudaErrorInvalidConfiguration;
+    return launch_sieve_kernel(g, b, sh, decoder == TSX_DEC_SPA_F32 ? 1 : 0, st);
+}
+
+bool decode_fits(const DevCode &g, int decoder) {
+    LaunchShape sh;
+    return plan(g, decoder, kLayScalar, 1, 1, 0, 1, &sh) && plan(g, decoder, kLaySieve, 1, 1, 0, 1, &sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -117,7 +160,7 @@ cudaError_t launch_compact(const EnumBuffers &b, long long n_rec, int *ts_off, i
     if (blocks > 4096) blocks = 4096;
     compact_kernel<<<blocks, 256, 0, st>>>(b, ts_off, ts_count, ts_thr, slot_map);
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || !b.record) return e;
+    if (e != cudaSuccess) return e;
     int rb = (int)((n_rec + 255) / 256);
     if (rb > 4096) rb = 4096;
     if (rb < 1) rb = 1;

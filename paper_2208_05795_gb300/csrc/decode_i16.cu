@@ -1,9 +1,10 @@
-// decode_i16.cu -- instantiation of the decoding kernel for DecNms16.
-#include "decode_impl.cuh"
+// decode_i16.cu -- the min-sum decoding kernels with int16 message storage.
+#include "decode_pair.cuh"
 
 namespace tsx {
-cudaError_t launch_enum_i16(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b,
-                            const LaunchShape &sh, cudaStream_t st) {
-    return launch_dec<DecNms16>(g, dp, b, sh, st);
+cudaError_t launch_nms16(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const LaunchShape &sh,
+                         bool pair, cudaStream_t st) {
+    if (pair) return launch_pair<false>(g, dp, b, sh, st);
+    return launch_scalar<DecNms16>(g, dp, b, sh, st);
 }
 }  // namespace tsx

@@ -1,9 +1,10 @@
-// decode_i8.cu -- instantiation of the decoding kernel for DecNms8.
-#include "decode_impl.cuh"
+// decode_i8.cu -- the min-sum decoding kernels with int8 message storage.
+#include "decode_pair.cuh"
 
 namespace tsx {
-cudaError_t launch_enum_i8(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b,
-                            const LaunchShape &sh, cudaStream_t st) {
-    return launch_dec<DecNms8>(g, dp, b, sh, st);
+cudaError_t launch_nms8(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const LaunchShape &sh,
+                         bool pair, cudaStream_t st) {
+    if (pair) return launch_pair<true>(g, dp, b, sh, st);
+    return launch_scalar<DecNms8>(g, dp, b, sh, st);
 }
 }  // namespace tsx

@@ -808,11 +808,10 @@ __global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, E
     uint32_t *xb = (uint32_t *)(slot + lay.xb_off);
 
     Decoder<Dec, DCMAX, QC> dec{g, sg, gp, dp, P, R};
-    Sieve<QC> sv{g, sg, gp};
 
     const long long total = (long long)b.ctr->n_cand_total;
     const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
-    long long my_dec = 0, my_it = 0, my_eu = 0, my_acyc = 0;
+    long long my_dec = 0, my_it = 0, my_eu = 0;
 
     lv Lbase;
     if constexpr (Dec::kFloat) Lbase = (lv)clampf_((float)dp.base_llr / 8.0f, -dp.spa_clip, dp.spa_clip);
@@ -886,79 +885,126 @@ __global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, E
         my_it += nit;
         my_eu += (long long)nit * g.E;
 
-        long long tslot = -1;
-        int flags = 0;
+        // records and the failing decode's x* for the sieve kernel
+        gp.sync();
+        const long long o = idx - b.cand_begin;
         if (failed) {
-            int *deg = (int *)R;
-            int a = 0;
-            gp.sync();
-            const int which = sv.run(xcur, xkeep, I, nI, deg, a);
-            flags = which;
-            if (which == 0) {
-                flags |= kFlagAcyclic;
-                my_acyc++;
-            } else {
-                int bb, elem;
-                sv.classify(deg, bb, elem);
-                gp.sync();
-                uint16_t *L = (uint16_t *)P;
-                uint16_t *key = (uint16_t *)R;
-                if (gp.gw == 0) {
-                    list_bits(xcur, g.n, L, lane);
-                    const int orbit = canon_key(g, L, a, xcur, key, misc->seg, lane);
-                    const int thr_ord = Dec::kFloat ? f2ord(thr_f) : thr;
-                    tslot = ts_insert(b, key, a, bb, orbit, elem | (which << 1), lane);
-                    if (tslot >= 0 && lane == 0) {
-                        atomicMin(&b.t_thr[tslot], thr_ord);
-                        atomicAdd(&b.t_count[tslot], 1);
-                    }
-                    if (tslot == -2) flags |= kFlagOverflow;
-                }
-                gp.sync();
-            }
+            uint32_t *dst = b.xstar + o * (long long)b.nw;
+            for (int w = gp.gt; w < b.nw; w += gp.T) dst[w] = xkeep[w];
         }
-        if (gp.gt == 0 && b.record) {
-            const long long o = idx - b.cand_begin;
+        if (gp.gt == 0) {
             b.c_thr[o] = thr;
             b.c_thr_f[o] = thr_f;
-            b.c_slot[o] = (int)(tslot >= 0 ? tslot : -1);
-            b.c_flags[o] = flags;
+            b.c_slot[o] = -1;
+            b.c_flags[o] = 0;
             b.c_decodes[o] = ndec;
             b.c_iters[o] = nit;
         }
+        gp.sync();
     }
     if (gp.gt == 0) {
         atomicAdd(&b.ctr->decodes, (unsigned long long)my_dec);
         atomicAdd(&b.ctr->iterations, (unsigned long long)my_it);
         atomicAdd(&b.ctr->edge_updates, (unsigned long long)my_eu);
-        atomicAdd(&b.ctr->acyclic, (unsigned long long)my_acyc);
     }
 }
 
+// ---------------------------------------------------------------------------
+// the sieve kernel: one warp per failing candidate
+// ---------------------------------------------------------------------------
+template <bool QC>
+__global__ void __launch_bounds__(512) sieve_kernel(DevCode g, EnumBuffers b, SlotLayout lay, int is_float) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SGraph sg = load_tables(g, smem);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *slot = smem + lay.tables_bytes + warp * lay.slot_bytes;
+    Misc *misc = (Misc *)(slot + lay.misc_off);
+    Grp gp;
+    gp.G = 1;
+    gp.T = 32;
+    gp.gw = 0;
+    gp.gt = lane;
+    gp.lane = lane;
+    gp.bar = 1;
+    gp.red = misc->red;
+    int *deg = (int *)(slot + lay.r_off);
+    uint16_t *key = (uint16_t *)(slot + lay.r_off);
+    uint16_t *L = (uint16_t *)(slot + lay.p_off);
+    uint32_t *S = (uint32_t *)(slot + lay.xa_off);
+    Sieve<QC> sv{g, sg, gp};
 
-// launches one instantiation (defined per decoder translation unit)
-template <class Dec, int DCMAX, bool QC>
-cudaError_t launch_t(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const LaunchShape &sh,
-                     cudaStream_t st) {
-    auto k = enum_kernel<Dec, DCMAX, QC>;
+    const long long total = (long long)b.ctr->n_cand_total;
+    const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
+    const long long n = end - b.cand_begin;
+    long long my_acyc = 0;
+    while (true) {
+        long long o = 0;
+        if (lane == 0) o = (long long)atomicAdd(&b.ctr->next_sieve, 1ull);
+        o = __shfl_sync(0xffffffffu, o, 0);
+        if (o >= n) break;
+        const bool failed = is_float ? b.c_thr_f[o] >= 0.0f : b.c_thr[o] >= 0;
+        if (!failed) continue;
+        const int4 I4 = b.cands[b.cand_begin + o];
+        int I[4] = {I4.x, I4.y, I4.z, I4.w};
+        const int nI = (I4.x >= 0) + (I4.y >= 0) + (I4.z >= 0) + (I4.w >= 0);
+        const uint32_t *xk = b.xstar + o * (long long)b.nw;
+        int a = 0;
+        const int which = sv.run(S, xk, I, nI, deg, a);
+        int flags = which;
+        long long tslot = -1;
+        if (which == 0) {
+            flags |= kFlagAcyclic;
+            my_acyc++;
+        } else {
+            int bb, elem;
+            sv.classify(deg, bb, elem);
+            __syncwarp();
+            list_bits(S, g.n, L, lane);
+            const int orbit = canon_key(g, L, a, S, key, misc->seg, lane);
+            const int thr_ord = is_float ? f2ord(b.c_thr_f[o]) : b.c_thr[o];
+            tslot = ts_insert(b, key, a, bb, orbit, elem | (which << 1), lane);
+            if (tslot >= 0 && lane == 0) {
+                atomicMin(&b.t_thr[tslot], thr_ord);
+                atomicAdd(&b.t_count[tslot], 1);
+            }
+            if (tslot == -2) flags |= kFlagOverflow;
+        }
+        if (lane == 0) {
+            b.c_slot[o] = (int)(tslot >= 0 ? tslot : -1);
+            b.c_flags[o] = flags;
+        }
+        __syncwarp();
+    }
+    if (lane == 0 && my_acyc) atomicAdd(&b.ctr->acyclic, (unsigned long long)my_acyc);
+}
+
+
+// launches one instantiation of a persistent kernel with every CTA resident
+template <class K, class... Args>
+cudaError_t launch_persistent(K k, const LaunchShape &sh, cudaStream_t st, Args... args) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem_bytes);
     if (e != cudaSuccess) return e;
     const int threads = sh.groups * sh.G * 32;
-    int occ = 0;  // persistent grid: every CTA resident at once
+    int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, sh.smem_bytes);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     if (sh.per_sm_req > 0 && sh.per_sm_req < occ) occ = sh.per_sm_req;
-    k<<<occ * sh.num_sms, threads, sh.smem_bytes, st>>>(g, dp, b, sh.lay, sh.G);
+    k<<<occ * sh.num_sms, threads, sh.smem_bytes, st>>>(args...);
     return cudaGetLastError();
 }
 
+// the scalar kernel (one codeword per group)
 template <class Dec>
-cudaError_t launch_dec(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const LaunchShape &sh,
-                       cudaStream_t st) {
+cudaError_t launch_scalar(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const LaunchShape &sh,
+                          cudaStream_t st) {
     const bool qc = g.kind == TSX_CODE_QC;
-    if (g.dc_max <= 8) return qc ? launch_t<Dec, 8, true>(g, dp, b, sh, st) : launch_t<Dec, 8, false>(g, dp, b, sh, st);
-    return qc ? launch_t<Dec, 32, true>(g, dp, b, sh, st) : launch_t<Dec, 32, false>(g, dp, b, sh, st);
+    if (g.dc_max <= 8)
+        return qc ? launch_persistent(enum_kernel<Dec, 8, true>, sh, st, g, dp, b, sh.lay, sh.G)
+                  : launch_persistent(enum_kernel<Dec, 8, false>, sh, st, g, dp, b, sh.lay, sh.G);
+    return qc ? launch_persistent(enum_kernel<Dec, 32, true>, sh, st, g, dp, b, sh.lay, sh.G)
+              : launch_persistent(enum_kernel<Dec, 32, false>, sh, st, g, dp, b, sh.lay, sh.G);
 }
 
 }  // namespace

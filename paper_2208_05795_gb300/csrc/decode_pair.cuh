@@ -1,0 +1,528 @@
+// decode_pair.cuh -- the fixed-point min-sum impulse decoder, two codewords
+// per lane.
+//
+// A group of G warps owns a pair of codeword slots ("halves" 0 and 1) and
+// runs two independent candidates at once: every shared-memory word holds
+// the same message or posterior of both codewords, one per 16-bit half, and
+// the two halves follow their own bisection and decode schedules (a half
+// whose decode ends starts its next decode at once; the other keeps going).
+//
+// Biased representation (so that one 32-bit add or subtract updates both
+// halves without a carry or borrow crossing between them, and signs and
+// equalities are single bits):
+//   message   R' = r + B                     B = 1024 (int16) / 128 (int8)
+//   posterior P' = P + beta                  beta = 0x8000
+//   channel   L'(v) = L_v + beta - dv(v) B   so P' = L' + sum_c R'
+//   extrinsic q' = P' - R' = q + beta - B    clamped to [beta - B - sat, beta - B + sat]
+//   then q'' = q' + B = clamp(q) + beta: bit 15 of each half is [q >= 0]
+//   magnitude a = max(q'', 2 beta - q'') = |q| + beta   (2 beta - x = ~x + 1 per half)
+// Every intermediate stays inside [0, 0xFFFF] per half for sat <= B and
+// (dv + 2) sat < 0x8000, which the launcher checks.  The arithmetic is the
+// same min-sum as the scalar decoder: r = sgn * ((alpha_num * min) >> alpha_shift)
+// over the other edges of the check, P = L + sum r, q = clamp(P - r).
+#pragma once
+#include <type_traits>
+
+#include "decode_impl.cuh"
+
+namespace tsx {
+namespace {
+
+__device__ __forceinline__ unsigned vmaxu2(unsigned a, unsigned b) {
+    unsigned d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned vminu2(unsigned a, unsigned b) {
+    unsigned d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned prmt(unsigned a, unsigned b, unsigned sel) {
+    unsigned d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+// 0xFFFF in each half whose bit 15 is set, else 0
+__device__ __forceinline__ unsigned spread15(unsigned x) { return prmt(x, x, 0xBB99u); }
+
+constexpr unsigned kBeta = 0x8000u;
+
+struct PairConst {
+    unsigned B2, BS2, LO2, HI2, BETA2, amask2;
+    int B, sat, an, as;
+};
+
+// per-half schedule state (uniform across the group)
+struct Half {
+    long long idx;  // candidate (absolute index), -1: idle
+    int I0, I1, I2, I3, nI;
+    int lo, hi, st, phase;  // bisection
+    int thr, ndec, nit;
+    int failed;
+    int Limp;  // channel LLR of the impulse nodes in the current decode
+    int k, ubest;
+    int first;  // current decode has run no check pass yet
+    int cur;    // x buffer of the current decode (0/1); keep = cur ^ 1
+    __device__ __forceinline__ int Ik(int t) const { return t == 0 ? I0 : t == 1 ? I1 : t == 2 ? I2 : I3; }
+};
+
+template <bool QC, int DC, bool EXACT, bool I8>
+struct PairDecoder {
+    static constexpr int RSZ = I8 ? 2 : 4;  // bytes of one packed message pair
+    const DevCode &g;
+    const SGraph &sg;
+    const Grp &gp;
+    const DecodeParams &dp;
+    const PairConst &pc;
+    unsigned char *Rb;  // packed messages, RSZ bytes per edge
+    unsigned *P;        // packed posteriors
+
+    __device__ __forceinline__ unsigned ldR(int byteoff) const {
+        if constexpr (I8) {
+            const unsigned x = *(const uint16_t *)(Rb + byteoff);
+            return prmt(x, 0u, 0x4140u);  // bytes b0, b1 -> halves
+        } else {
+            return *(const unsigned *)(Rb + byteoff);
+        }
+    }
+    __device__ __forceinline__ void stR(int byteoff, unsigned v) const {
+        if constexpr (I8) *(uint16_t *)(Rb + byteoff) = (uint16_t)prmt(v, 0u, 0x0020u);
+        else *(unsigned *)(Rb + byteoff) = v;
+    }
+
+    // One check node.  pv(p): byte offset of P'[v_p]; re(p): byte offset of
+    // R'[e_p].  Returns the unsatisfied flags of both halves in bits 0/1.
+    template <class PV, class RE>
+    __device__ __forceinline__ int check_node(int deg, unsigned km, unsigned kb, bool writeR, PV pv, RE re) const {
+        unsigned sp = 0, sx = 0, m1 = pc.BS2, m2 = pc.BS2;
+        unsigned qs[DC], as_[DC];
+#pragma unroll
+        for (int p = 0; p < DC; p++) {
+            if (EXACT || p < deg) {
+                const unsigned x = *(const unsigned *)((const unsigned char *)P + pv(p));
+                const unsigned y = (ldR(re(p)) & km) | kb;
+                sp ^= x;
+                unsigned q = x - y;
+                q = vminu2(vmaxu2(q, pc.LO2), pc.HI2) + pc.B2;
+                sx ^= q;
+                const unsigned a = vmaxu2(q, (~q) + 0x00010001u);
+                m2 = vminu2(m2, vmaxu2(m1, a));
+                m1 = vminu2(m1, a);
+                qs[p] = q;
+                as_[p] = a;
+            }
+        }
+        // syndrome bit of each half: sp bit 15 = parity of #(P >= 0), and
+        // #(P < 0) = deg - #(P >= 0)
+        const unsigned dodd = (deg & 1) ? 0x80008000u : 0u;
+        const unsigned unsat = (sp ^ dodd) & 0x80008000u;
+        if (writeR) {
+            const unsigned d1 = m1 - pc.BETA2, d2 = m2 - pc.BETA2;
+            const unsigned o1 = ((d1 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o2 = ((d2 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            // bit 15 of sx ^ q_p = parity of #(q >= 0) over the other edges;
+            // negatives among the others = (deg - 1) - that
+            const unsigned kodd = ((deg - 1) & 1) ? 0x80008000u : 0u;
+#pragma unroll
+            for (int p = 0; p < DC; p++) {
+                if (EXACT || p < deg) {
+                    const unsigned neg = spread15(sx ^ qs[p] ^ kodd);       // 0xFFFF: others' sign product < 0
+                    const unsigned ne = spread15(as_[p] - m1 + 0x7FFF7FFFu);  // 0xFFFF: |q_p| != min1
+                    const unsigned mag = (o1 & ne) | (o2 & ~ne);
+                    const unsigned pos = pc.B2 + mag, ng = pc.B2 - mag;
+                    stR(re(p), (ng & neg) | (pos & ~neg));
+                }
+            }
+        }
+        return (int)(((unsat >> 15) & 1u) | ((unsat >> 30) & 2u));
+    }
+
+    // check pass; returns u of half 0 in the low 16 bits and half 1 above
+    __device__ __forceinline__ int check_pass(unsigned km, unsigned kb, bool writeR) const {
+        int u0 = 0, u1 = 0;
+        const int Z = g.Z;
+        if constexpr (QC) {
+            for (int i = 0; i < g.m_b; i++) {
+                const int deg = EXACT ? DC : sg.rdeg[i];
+                const int rb = sg.reoff[i] * RSZ;
+                if constexpr (DC <= 8) {  // the row block's shifts in registers
+                    int rjz4[DC], rsh[DC], pz[DC];
+#pragma unroll
+                    for (int p = 0; p < DC; p++) {
+                        if (EXACT || p < deg) {
+                            rjz4[p] = sg.rjz[i * g.dc_max + p] * 4;
+                            rsh[p] = sg.rs[i * g.dc_max + p];
+                            pz[p] = p * Z * RSZ;
+                        }
+                    }
+                    for (int r = gp.gt; r < Z; r += gp.T) {
+                        const int f = check_node(
+                            deg, km, kb, writeR,
+                            [&](int p) {
+                                const int t = r + rsh[p];
+                                return rjz4[p] + 4 * (int)min((unsigned)t, (unsigned)(t - Z));
+                            },
+                            [&](int p) { return rb + pz[p] + r * RSZ; });
+                        u0 += f & 1;
+                        u1 += f >> 1;
+                    }
+                } else {
+                    const int32_t *rjz = sg.rjz + i * g.dc_max;
+                    const int16_t *rs = sg.rs + i * g.dc_max;
+                    for (int r = gp.gt; r < Z; r += gp.T) {
+                        const int f = check_node(
+                            deg, km, kb, writeR,
+                            [&](int p) {
+                                const int t = r + rs[p];
+                                return 4 * (rjz[p] + (int)min((unsigned)t, (unsigned)(t - Z)));
+                            },
+                            [&](int p) { return rb + (p * Z + r) * RSZ; });
+                        u0 += f & 1;
+                        u1 += f >> 1;
+                    }
+                }
+            }
+        } else {
+            for (int c = gp.gt; c < g.m; c += gp.T) {
+                const int e0 = sg.c_ptr[c];
+                const int deg = EXACT ? DC : sg.c_ptr[c + 1] - e0;
+                const int f = check_node(
+                    deg, km, kb, writeR, [&](int p) { return 4 * (int)sg.c_vn[e0 + p]; },
+                    [&](int p) { return (e0 + p) * RSZ; });
+                u0 += f & 1;
+                u1 += f >> 1;
+            }
+        }
+        const int s = gp.sum(u0 | (u1 << 16));
+        return s;
+    }
+
+    // channel value L'(v) of a non-impulse node, packed for both halves
+    __device__ __forceinline__ unsigned lbase2(int dv, int Lb) const {
+        const unsigned l = (unsigned)(Lb + (int)kBeta - dv * pc.B);
+        return l | (l << 16);
+    }
+
+    // posterior pass (both halves): P' = L' + sum R'
+    __device__ __forceinline__ void vn_pass(int Lb) const {
+        const int Z = g.Z;
+        if constexpr (QC) {
+            for (int j = 0; j < g.n_b; j++) {
+                const int dv = sg.cdeg[j];
+                const unsigned l2 = lbase2(dv, Lb);
+                if (dv <= 4) {
+                    int ce[4], csh[4];
+#pragma unroll
+                    for (int t = 0; t < 4; t++)
+                        if (t < dv) {
+                            ce[t] = sg.ceoff[j * g.dv_max + t] * RSZ;
+                            csh[t] = sg.cs[j * g.dv_max + t];
+                        }
+                    for (int k = gp.gt; k < Z; k += gp.T) {
+                        unsigned acc = l2;
+#pragma unroll
+                        for (int t = 0; t < 4; t++)
+                            if (t < dv) {
+                                const int rr = k - csh[t];
+                                acc += ldR(ce[t] + RSZ * (int)min((unsigned)rr, (unsigned)(rr + Z)));
+                            }
+                        P[j * Z + k] = acc;
+                    }
+                } else {
+                    for (int k = gp.gt; k < Z; k += gp.T) {
+                        unsigned acc = l2;
+                        for (int t = 0; t < dv; t++) {
+                            const int idx = j * g.dv_max + t;
+                            const int rr = k - sg.cs[idx];
+                            acc += ldR(sg.ceoff[idx] * RSZ + RSZ * (int)min((unsigned)rr, (unsigned)(rr + Z)));
+                        }
+                        P[j * Z + k] = acc;
+                    }
+                }
+            }
+        } else {
+            for (int v = gp.gt; v < g.n; v += gp.T) {
+                const int t0 = sg.v_ptr[v], t1 = sg.v_ptr[v + 1];
+                unsigned acc = lbase2(t1 - t0, Lb);
+                for (int t = t0; t < t1; t++) acc += ldR(sg.v_edge[t] * RSZ);
+                P[v] = acc;
+            }
+        }
+    }
+
+    __device__ __forceinline__ int vdeg(int v) const {
+        if constexpr (QC) return sg.cdeg[v / g.Z];
+        else return sg.v_ptr[v + 1] - sg.v_ptr[v];
+    }
+
+    // half h of P'[v] for an impulse node: L + beta before the first check
+    // pass, else L' + the sum of its half's messages
+    __device__ __forceinline__ unsigned half_post(int v, int h, int L, bool with_msgs) const {
+        if (!with_msgs) return (unsigned)(L + (int)kBeta) & 0xFFFFu;
+        const int dv = vdeg(v);
+        unsigned acc = (unsigned)(L + (int)kBeta - dv * pc.B);
+        {
+            for (int t = 0; t < dv; t++) {
+                int e;
+                if constexpr (QC) {
+                    const int j = v / g.Z, k = v - j * g.Z;
+                    const int idx = j * g.dv_max + t;
+                    e = sg.ceoff[idx] + wrapZneg(k - sg.cs[idx], g.Z);
+                } else {
+                    e = sg.v_edge[sg.v_ptr[v] + t];
+                }
+                acc += (ldR(e * RSZ) >> (16 * h)) & 0xFFFFu;
+            }
+        }
+        return acc & 0xFFFFu;
+    }
+
+    __device__ __forceinline__ void set_half(int v, int h, unsigned val) const {
+        ((uint16_t *)P)[2 * v + h] = (uint16_t)val;
+    }
+
+    // x_k of half h (P < 0, i.e. bit 15 of the half clear) into a bitmask
+    __device__ __forceinline__ void save_x(int h, uint32_t *xw) const {
+        const unsigned bitpos = 15u + 16u * h;
+        for (int base = 0; base < g.n; base += gp.T) {
+            const int v = base + gp.gt;
+            const bool bit = v < g.n && !((P[v] >> bitpos) & 1u);
+            const unsigned w = __ballot_sync(0xffffffffu, bit);
+            const int wi = (base >> 5) + gp.gw;
+            if (gp.lane == 0 && (wi << 5) < g.n) xw[wi] = w;
+        }
+    }
+
+    __device__ __forceinline__ int any_neg(int h) const {
+        const unsigned bitpos = 15u + 16u * h;
+        int neg = 0;
+        for (int v = gp.gt; v < g.n; v += gp.T) neg |= !((P[v] >> bitpos) & 1u);
+        return gp.sum(neg);
+    }
+};
+
+template <bool QC, int DC, bool EXACT, bool I8>
+__global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay,
+                                                   int G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SGraph sg = load_tables(g, smem);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = warp / G;
+    unsigned char *slot = smem + lay.tables_bytes + grp * lay.slot_bytes;
+    Misc *misc = (Misc *)(slot + lay.misc_off);
+    Grp gp;
+    gp.G = G;
+    gp.T = 32 * G;
+    gp.gw = warp - grp * G;
+    gp.gt = gp.gw * 32 + lane;
+    gp.lane = lane;
+    gp.bar = 1 + grp;
+    gp.red = misc->red;
+    unsigned char *Rb = slot + lay.r_off;
+    unsigned *P = (unsigned *)(slot + lay.p_off);
+    const int nw = (g.n + 31) >> 5;
+    uint32_t *xb = (uint32_t *)(slot + lay.xa_off);  // 4 buffers of nw words: [half][cur/keep]
+    const int xstride = (nw + 3) & ~3;
+
+    PairConst pc;
+    pc.B = I8 ? 128 : 1024;
+    pc.sat = dp.sat;
+    pc.an = dp.alpha_num;
+    pc.as = dp.alpha_shift;
+    pc.B2 = (unsigned)pc.B * 0x00010001u;
+    pc.BETA2 = kBeta * 0x00010001u;
+    pc.BS2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
+    pc.LO2 = (kBeta - (unsigned)pc.B - (unsigned)pc.sat) * 0x00010001u;
+    pc.HI2 = (kBeta - (unsigned)pc.B + (unsigned)pc.sat) * 0x00010001u;
+    pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
+    PairDecoder<QC, DC, EXACT, I8> dec{g, sg, gp, dp, pc, Rb, P};
+
+    const long long total = (long long)b.ctr->n_cand_total;
+    const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
+    const int Lb = clampi(dp.base_llr, -dp.sat, dp.sat);
+    const int amax = (1 << dp.amp_steps) - 1;
+    long long my_dec = 0, my_it = 0;
+
+    Half H[2];
+
+    auto fetch = [&](Half &h) {
+        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(&b.ctr->next_cand, 1ull);
+        gp.sync();
+        const long long idx = b.cand_begin + misc->bcast[0];
+        gp.sync();
+        if (idx >= end) {
+            h.idx = -1;
+            return;
+        }
+        const int4 I4 = b.cands[idx];
+        h.idx = idx;
+        h.I0 = I4.x; h.I1 = I4.y; h.I2 = I4.z; h.I3 = I4.w;
+        h.nI = (I4.x >= 0) + (I4.y >= 0) + (I4.z >= 0) + (I4.w >= 0);
+        h.lo = 0; h.hi = amax; h.st = 0; h.phase = 0;
+        h.thr = -1; h.ndec = 0; h.nit = 0; h.failed = 0;
+        h.cur = 0;
+        h.Limp = clampi(dp.base_llr - amax, -dp.sat, dp.sat);
+    };
+    // finish candidate of half hh (records, x* to global) and fetch the next
+    auto finish = [&](Half &h, int hh) {
+        gp.sync();
+        const long long o = h.idx - b.cand_begin;
+        if (h.failed) {
+            const uint32_t *src = xb + (2 * hh + (h.cur ^ 1)) * xstride;
+            uint32_t *dst = b.xstar + o * (long long)b.nw;
+            for (int w = gp.gt; w < nw; w += gp.T) dst[w] = src[w];
+        }
+        if (gp.gt == 0) {
+            b.c_thr[o] = h.failed ? h.thr : -1;
+            b.c_thr_f[o] = -1.0f;
+            b.c_slot[o] = -1;
+            b.c_flags[o] = 0;
+            b.c_decodes[o] = h.ndec;
+            b.c_iters[o] = h.nit;
+        }
+        my_dec += h.ndec;
+        my_it += h.nit;
+        fetch(h);
+    };
+    // Advance half hh past trivial decodes (impulse LLR >= 0: every hard
+    // decision 0, u_0 = 0, success at iteration 0) until a decode that needs
+    // iterations is set up in h (returns true) or no candidate is left.
+    auto settle = [&](Half &h, int hh) {
+        while (h.idx >= 0) {
+            if (h.Limp < 0) return true;
+            // trivial success
+            h.ndec++;
+            if (h.phase == 0) {
+                finish(h, hh);  // no failure at the largest amplitude
+                continue;
+            }
+            h.lo = (h.lo + h.hi) >> 1;  // the decode at mid succeeded
+            if (h.st < dp.amp_steps && h.hi - h.lo > 1) {
+                const int mid = (h.lo + h.hi) >> 1;
+                h.st++;
+                h.Limp = clampi(dp.base_llr - mid, -dp.sat, dp.sat);
+            } else {
+                h.thr = h.hi;
+                finish(h, hh);
+            }
+        }
+        return false;
+    };
+    // (re)initialize half hh of P' for a new decode
+    auto start = [&](Half &h, int hh) {
+        for (int base = 0; base < g.n; base += gp.T) {
+            const int v = base + gp.gt;
+            if (v < g.n) dec.set_half(v, hh, (unsigned)(Lb + (int)kBeta));
+        }
+        gp.sync();
+        if (gp.gt < h.nI) {
+            const int t = h.Ik(gp.gt);
+            dec.set_half(t, hh, dec.half_post(t, hh, h.Limp, false));
+        }
+        gp.sync();
+        h.k = 0;
+        h.ubest = 0x7fffffff;
+        h.first = 1;
+    };
+
+    for (int hh = 0; hh < 2; hh++) {
+        fetch(H[hh]);
+        if (settle(H[hh], hh)) start(H[hh], hh);
+    }
+
+    while (H[0].idx >= 0 || H[1].idx >= 0) {
+        const unsigned km = (H[0].first ? 0xFFFF0000u : 0xFFFFFFFFu) & (H[1].first ? 0x0000FFFFu : 0xFFFFFFFFu);
+        const unsigned kb = pc.B2 & ~km;
+        const bool wr = (H[0].idx >= 0 && H[0].k < dp.K) || (H[1].idx >= 0 && H[1].k < dp.K);
+        const int us = dec.check_pass(km, kb, wr);
+        int restart[2] = {0, 0};
+        for (int hh = 0; hh < 2; hh++) {
+            Half &h = H[hh];
+            if (h.idx < 0) continue;
+            const int u = hh == 0 ? (us & 0xFFFF) : (us >> 16);
+            uint32_t *xc = xb + (2 * hh + h.cur) * xstride;
+            if (h.k >= g.wstart && u < h.ubest) {
+                h.ubest = u;
+                dec.save_x(hh, xc);
+            }
+            if (u != 0 && h.k != dp.K) continue;
+            // the decode ended at K_last = k
+            const int kl = h.k;
+            if (kl < g.wstart) dec.save_x(hh, xc);
+            const bool fail = u != 0 || dec.any_neg(hh) != 0;
+            h.ndec++;
+            h.nit += kl;
+            if (h.phase == 0) {
+                if (!fail) {
+                    finish(h, hh);
+                } else {
+                    h.failed = 1;
+                    h.cur ^= 1;
+                    h.phase = 1;
+                }
+            } else {
+                const int mid = (h.lo + h.hi) >> 1;
+                if (fail) {
+                    h.hi = mid;
+                    h.cur ^= 1;
+                } else {
+                    h.lo = mid;
+                }
+            }
+            if (h.idx >= 0 && h.phase == 1) {
+                if (h.st < dp.amp_steps && h.hi - h.lo > 1) {
+                    const int mid = (h.lo + h.hi) >> 1;
+                    h.st++;
+                    h.Limp = clampi(dp.base_llr - mid, -dp.sat, dp.sat);
+                } else {
+                    h.thr = h.hi;
+                    finish(h, hh);
+                }
+            }
+            restart[hh] = 1;
+        }
+        const bool cont0 = H[0].idx >= 0 && !restart[0], cont1 = H[1].idx >= 0 && !restart[1];
+        if (cont0 || cont1) {
+            dec.vn_pass(Lb);
+            gp.sync();
+            for (int hh = 0; hh < 2; hh++) {
+                Half &h = H[hh];
+                if (!(hh == 0 ? cont0 : cont1)) continue;
+                if (gp.gt < h.nI) {
+                    const int t = h.Ik(gp.gt);
+                    dec.set_half(t, hh, dec.half_post(t, hh, h.Limp, true));
+                }
+                h.k++;
+                h.first = 0;
+            }
+            gp.sync();
+        }
+        for (int hh = 0; hh < 2; hh++)
+            if (restart[hh] && settle(H[hh], hh)) start(H[hh], hh);
+    }
+    if (gp.gt == 0) {
+        atomicAdd(&b.ctr->decodes, (unsigned long long)my_dec);
+        atomicAdd(&b.ctr->iterations, (unsigned long long)my_it);
+        atomicAdd(&b.ctr->edge_updates, (unsigned long long)my_it * (unsigned long long)g.E);
+    }
+}
+
+template <bool I8>
+cudaError_t launch_pair(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const LaunchShape &sh,
+                        cudaStream_t st) {
+    const bool qc = g.kind == TSX_CODE_QC;
+    const bool reg6 = g.dc_min == 6 && g.dc_max == 6;
+    if (reg6)
+        return qc ? launch_persistent(pair_kernel<true, 6, true, I8>, sh, st, g, dp, b, sh.lay, sh.G)
+                  : launch_persistent(pair_kernel<false, 6, true, I8>, sh, st, g, dp, b, sh.lay, sh.G);
+    if (g.dc_max <= 8)
+        return qc ? launch_persistent(pair_kernel<true, 8, false, I8>, sh, st, g, dp, b, sh.lay, sh.G)
+                  : launch_persistent(pair_kernel<false, 8, false, I8>, sh, st, g, dp, b, sh.lay, sh.G);
+    return qc ? launch_persistent(pair_kernel<true, 32, false, I8>, sh, st, g, dp, b, sh.lay, sh.G)
+              : launch_persistent(pair_kernel<false, 32, false, I8>, sh, st, g, dp, b, sh.lay, sh.G);
+}
+
+}  // namespace
+}  // namespace tsx

@@ -53,14 +53,20 @@ struct LaunchShape {
     SlotLayout lay;
 };
 
-// Computes the slot layout for a decoder and picks a shape: G warps per
-// codeword (0 = automatic) and groups per CTA (0 = automatic); ctas_per_sm
-// 0 = as many as fit.  Returns false if one codeword does not fit.
-bool plan_shape(const DevCode &g, int decoder, int G, int groups, int ctas_per_sm, int num_sms,
-                LaunchShape *out);
+// Runs the impulse decodes with bisection over the candidates of b and
+// writes the per-candidate records and x* of failing candidates.  NMS
+// decoders use the two-codeword kernel where its 16-bit bias bounds hold
+// (else, or with force_scalar, the one-codeword kernel).  G / groups /
+// ctas_per_sm: 0 = automatic.
+cudaError_t launch_decode(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, int G, int groups,
+                          int ctas_per_sm, int num_sms, int force_scalar, cudaStream_t st);
 
-cudaError_t launch_enum(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b,
-                        const LaunchShape &sh, cudaStream_t st);
+// Sieve (Tree / TS), classification, canonical key and hash insert of every
+// failing candidate (reads the records and x* written by the decoder).
+cudaError_t launch_sieve(const DevCode &g, const EnumBuffers &b, int decoder, int num_sms, cudaStream_t st);
+
+// Whether one codeword of g fits the shared memory of a CTA.
+bool decode_fits(const DevCode &g, int decoder);
 
 // Compacts the hash table: assigns each stored trapping set an index,
 // writes its pool offset / count / min threshold, and rewrites the

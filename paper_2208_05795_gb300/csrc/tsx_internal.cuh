@@ -28,6 +28,7 @@ struct DevCode {
     int kind;  // TSX_CODE_QC / TSX_CODE_CSR
     int n, m, E, Z, n_b, m_b;
     int dv_max, dc_max;
+    int dc_min;         // smallest check degree (dc_min == dc_max: check-regular)
     int girth, wstart;  // wstart = max(1, girth/2)
     int n_rep;
     // QC tables
@@ -59,6 +60,7 @@ struct Counters {
     unsigned long long pool_top;    // int32 words used in the key pool
     unsigned long long n_cand_total;  // canonical candidates written
     unsigned long long acyclic;
+    unsigned long long next_sieve;  // work queue of the sieve kernel
     unsigned int n_ts;
     unsigned int err;               // bit flags, see kErr*
 };
@@ -90,7 +92,7 @@ struct EnumBuffers {
     const int4 *cands;        // canonical candidate sets, -1 padded
     long long cand_begin;     // first candidate to decode
     long long cand_end;       // one past the last (clamped to the total on device)
-    int record;               // write per-candidate records
+    int record;               // (unused on the device: records are always kept)
     // per-candidate outputs, indexed by (candidate - cand_begin)
     int *c_thr;
     float *c_thr_f;
@@ -98,6 +100,9 @@ struct EnumBuffers {
     int *c_flags;
     int *c_decodes;
     int *c_iters;
+    // best error pattern x* of every failing candidate, nw words each
+    uint32_t *xstar;
+    int nw;
     // trapping-set hash table
     unsigned long long *tags;  // [cap] (hash_hi32 << 32) | pool offset, 0 = empty
     int *t_thr;                // [cap] min threshold, int-ordered

@@ -68,7 +68,8 @@ def test_qc96_stats(qc96):
 
 def test_qc96_deterministic_and_shape_independent(qc96):
     w, g, res, v = qc96
-    for over in (dict(), dict(warps_per_cta=1), dict(warps_per_cta=4, ctas_per_sm=1)):
+    for over in (dict(), dict(warps_per_cta=1), dict(warps_per_cta=4, ctas_per_sm=1), dict(kernel=1),
+                 dict(kernel=1, warps_per_cta=2), dict(kernel=2, warps_per_cta=2)):
         v2 = run_lib(w["code"], **_params(w, **over))
         assert lib_records(v2) == lib_records(v)
         assert lib_ts(v2) == lib_ts(v)
@@ -86,24 +87,28 @@ def test_qc96_shards(qc96):
         assert all(full[t] == r for t, r in lib_records(vs).items())
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("over", [dict(max_size=1), dict(max_size=2), dict(K=0), dict(amp_steps=1),
-                                  dict(K=7, base_llr=40, alpha_num=5, alpha_shift=3), dict(sat=63)])
-def test_qc96_parameter_edges(over):
+                                  dict(K=7, base_llr=40, alpha_num=5, alpha_shift=3), dict(sat=63),
+                                  dict(base_llr=2000, sat=1023)])
+def test_qc96_parameter_edges(over, kernel):
+    # kernel 1: one codeword per group; kernel 2: two per lane (16-bit halves)
     w = synth.workload("qc96")
     g = oracle.Graph(w["code"])
     p = _params(w, **over)
     res = g.enumerate(**p)
-    v = run_lib(w["code"], **p)
+    v = run_lib(w["code"], kernel=kernel, **p)
     _full_compare(v, res)
 
 
-def test_qc96_int8_storage_bit_exact():
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_qc96_int8_storage_bit_exact(kernel):
     # int8 check-to-variable storage is the same decoder with sat <= 169
     w = synth.workload("qc96")
     g = oracle.Graph(w["code"])
     p = _params(w, sat=127)
     res = g.enumerate(**p)
-    v = run_lib(w["code"], decoder="nms8", **p)
+    v = run_lib(w["code"], decoder="nms8", kernel=kernel, **p)
     _full_compare(v, res)
 
 
