@@ -148,15 +148,26 @@ def test_planted_codeword_and_tree_code():
 
 
 def test_code1_table5_small_sets():
-    # Table V's Code 1 has one 4-cycle orbit: impulses on its two VNs report TS(2,2)
+    # Table V's Code 1 has one 4-cycle orbit; the impulse on its two VNs
+    # reports TS(2,2).  Full library run, oracle on a sample that includes it.
     E, Z, _ = helpers.load_code1()
     code = synth.qc_code(E, Z)
+    w = dict(code=code, K=20, base_llr=16, amp_steps=10, max_size=2, cycle_len=0)
+    v = run_lib(code, **_params(w))
     g = oracle.Graph(code)
-    p = dict(K=20, base_llr=16, amp_steps=10, max_size=2)
-    res = g.enumerate(**p)
-    v = run_lib(code, **p)
-    _full_compare(v, res)
-    assert any(a == 2 and b == 2 for a, b, *_ in lib_ts(v).values())
+    H = g.dense().astype(np.int64)
+    pair = None
+    for u in g.ball4(0):
+        if int((H[:, 0] * H[:, u]).sum()) >= 2:
+            pair = g.canon([0, int(u)])[0]
+    assert pair is not None
+    res = g.enumerate(np.array([[2, pair[0], pair[1], -1, -1]], np.int32), **_params(w))
+    assert (res.ts_list[res.ts[0]].a, res.ts_list[res.ts[0]].b) == (2, 2)
+    i = lib_cand_tuples(v).index(pair)
+    assert int(v["cand_thr"][i]) == int(res.thr[0])
+    k = v["keys"][int(v["cand_ts"][i])]
+    assert k == res.ts_list[res.ts[0]].key and len(k) == 2
+    _sampled_compare(w, v, 30, seed=13)
 
 
 def test_batch_code_with_zero_blocks():
