@@ -168,6 +168,8 @@ int build_csr(const tsx_code_desc &d, HostTables &h) {
     if (h.dc_max > TSX_MAX_DC || h.dv_max > TSX_MAX_DV) return TSX_EUNSUPPORTED;
     h.v_ptr.assign(d.n + 1, 0);
     for (int v = 0; v < d.n; v++) h.v_ptr[v + 1] = (uint16_t)(h.v_ptr[v] + vd[v]);
+    // messages are stored position-major: edge (c, p) at p*m + c
+    if ((long long)h.dc_max * d.m > 65535) return TSX_EUNSUPPORTED;
     h.v_edge.resize(E);
     h.v_chk.resize(E);
     std::vector<int> fill(d.n, 0);
@@ -175,7 +177,7 @@ int build_csr(const tsx_code_desc &d, HostTables &h) {
         for (int e = h.c_ptr[c]; e < h.c_ptr[c + 1]; e++) {
             int v = h.c_vn[e];
             int t = h.v_ptr[v] + fill[v]++;
-            h.v_edge[t] = (uint16_t)e;
+            h.v_edge[t] = (uint16_t)((e - h.c_ptr[c]) * d.m + c);
             h.v_chk[t] = (uint16_t)c;
         }
     return TSX_OK;

@@ -25,17 +25,19 @@ SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
     SlotLayout L{};
     L.tables_bytes = al16(tab_offsets(g).total);
     const int nw = (g.n + 31) / 32;
+    // message slots: QC edges, or the position-major m x dc_max grid of a CSR code
+    const int nmsg = g.kind == TSX_CODE_QC ? g.E : g.m * g.dc_max;
     int x = 0;
     if (kind == kLayScalar) {
-        L.r_off = x; x += al16(g.E * msg_bytes(decoder));
+        L.r_off = x; x += al16(nmsg * msg_bytes(decoder));
         L.p_off = x; x += al16(g.n * post_bytes(decoder));
         L.xa_off = x; x += al16(nw * 4);
         L.xb_off = x; x += al16(nw * 4);
     } else if (kind == kLayPair) {
         const int rsz = decoder == TSX_DEC_NMS_I8 ? 2 : 4;
         const int xstride = (nw + 3) & ~3;
-        L.r_off = x; x += al16(g.E * rsz);
-        L.p_off = x; x += al16(g.n * 4);
+        L.r_off = x; x += al16(nmsg * rsz);
+        L.p_off = x; x += al16(2 * g.n * 4);  // current and accumulating posteriors
         L.xa_off = x; x += al16(4 * xstride * 4);
         L.xb_off = L.xa_off;
     } else {

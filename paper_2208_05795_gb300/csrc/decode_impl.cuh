@@ -285,7 +285,8 @@ struct Decoder {
             for (int c = gp.gt; c < g.m; c += gp.T) {
                 const int e0 = sg.c_ptr[c];
                 const int deg = sg.c_ptr[c + 1] - e0;
-                unsat += check_node(first, writeR, deg, e0, 1, [&](int p) { return (int)sg.c_vn[e0 + p]; });
+                // message (c, p) lives at p*m + c (consecutive lanes, consecutive words)
+                unsat += check_node(first, writeR, deg, c, g.m, [&](int p) { return (int)sg.c_vn[e0 + p]; });
             }
         }
         return gp.sum(unsat);

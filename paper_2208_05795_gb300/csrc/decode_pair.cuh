@@ -16,13 +16,17 @@
 //   extrinsic q' = P' - R' = q + beta - B    clamped to [beta - B - sat, beta - B + sat]
 //   then q'' = q' + B = clamp(q) + beta: bit 15 of each half is [q >= 0]
 //   magnitude a = max(q'', 2 beta - q'') = |q| + beta   (2 beta - x = ~x + 1 per half)
-// Every intermediate stays inside [0, 0xFFFF] per half for sat <= B and
-// (dv + 2) sat < 0x8000, which the launcher checks.  The arithmetic is the
-// same min-sum as the scalar decoder: r = sgn * ((alpha_num * min) >> alpha_shift)
+// Every intermediate stays inside [0, 0xFFFF] per half for rmax <= B and
+// (dv + 2) sat <= beta - B, which the launcher checks; both halves always
+// hold values of a valid decode (an idle half keeps decoding its last input)
+// so that neither can carry into the other.  The arithmetic is the same
+// min-sum as the scalar decoder: r = sgn * ((alpha_num * min) >> alpha_shift)
 // over the other edges of the check, P = L + sum r, q = clamp(P - r).
+//
+// No variable-node pass: each check adds its new messages into the next
+// posterior buffer with shared-memory atomic adds (exact and order-free on
+// the biased words); that buffer starts at L' with the impulse values in it.
 #pragma once
-#include <type_traits>
-
 #include "decode_impl.cuh"
 
 namespace tsx {
@@ -45,6 +49,10 @@ __device__ __forceinline__ unsigned prmt(unsigned a, unsigned b, unsigned sel) {
 }
 // 0xFFFF in each half whose bit 15 is set, else 0
 __device__ __forceinline__ unsigned spread15(unsigned x) { return prmt(x, x, 0xBB99u); }
+__device__ __forceinline__ void red_add(unsigned char *addr, unsigned v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(addr)), "r"(v)
+                 : "memory");
+}
 
 constexpr unsigned kBeta = 0x8000u;
 
@@ -73,10 +81,8 @@ struct PairDecoder {
     const DevCode &g;
     const SGraph &sg;
     const Grp &gp;
-    const DecodeParams &dp;
     const PairConst &pc;
     unsigned char *Rb;  // packed messages, RSZ bytes per edge
-    unsigned *P;        // packed posteriors
 
     __device__ __forceinline__ unsigned ldR(int byteoff) const {
         if constexpr (I8) {
@@ -92,15 +98,19 @@ struct PairDecoder {
     }
 
     // One check node.  pv(p): byte offset of P'[v_p]; re(p): byte offset of
-    // R'[e_p].  Returns the unsatisfied flags of both halves in bits 0/1.
+    // R'[e_p].  Reads Pc, adds the new messages into Pn.  Returns the
+    // unsatisfied flags of both halves in bits 0/1.
     template <class PV, class RE>
-    __device__ __forceinline__ int check_node(int deg, unsigned km, unsigned kb, bool writeR, PV pv, RE re) const {
+    __device__ __forceinline__ int check_node(int deg, unsigned km, unsigned kb, bool writeR, const unsigned char *Pc,
+                                              unsigned char *Pn, PV pv, RE re) const {
         unsigned sp = 0, sx = 0, m1 = pc.BS2, m2 = pc.BS2;
         unsigned qs[DC], as_[DC];
+        int po[DC];
 #pragma unroll
         for (int p = 0; p < DC; p++) {
             if (EXACT || p < deg) {
-                const unsigned x = *(const unsigned *)((const unsigned char *)P + pv(p));
+                po[p] = pv(p);
+                const unsigned x = *(const unsigned *)(Pc + po[p]);
                 const unsigned y = (ldR(re(p)) & km) | kb;
                 sp ^= x;
                 unsigned q = x - y;
@@ -127,11 +137,13 @@ struct PairDecoder {
 #pragma unroll
             for (int p = 0; p < DC; p++) {
                 if (EXACT || p < deg) {
-                    const unsigned neg = spread15(sx ^ qs[p] ^ kodd);       // 0xFFFF: others' sign product < 0
+                    const unsigned neg = spread15(sx ^ qs[p] ^ kodd);        // 0xFFFF: others' sign product < 0
                     const unsigned ne = spread15(as_[p] - m1 + 0x7FFF7FFFu);  // 0xFFFF: |q_p| != min1
                     const unsigned mag = (o1 & ne) | (o2 & ~ne);
                     const unsigned pos = pc.B2 + mag, ng = pc.B2 - mag;
-                    stR(re(p), (ng & neg) | (pos & ~neg));
+                    const unsigned rn = (ng & neg) | (pos & ~neg);
+                    stR(re(p), rn);
+                    red_add(Pn + po[p], rn);
                 }
             }
         }
@@ -139,8 +151,11 @@ struct PairDecoder {
     }
 
     // check pass; returns u of half 0 in the low 16 bits and half 1 above
-    __device__ __forceinline__ int check_pass(unsigned km, unsigned kb, bool writeR) const {
+    __device__ __forceinline__ int check_pass(unsigned km, unsigned kb, bool writeR, const unsigned *Pcur,
+                                              unsigned *Pnext) const {
         int u0 = 0, u1 = 0;
+        const unsigned char *Pc = (const unsigned char *)Pcur;
+        unsigned char *Pn = (unsigned char *)Pnext;
         const int Z = g.Z;
         if constexpr (QC) {
             for (int i = 0; i < g.m_b; i++) {
@@ -158,7 +173,7 @@ struct PairDecoder {
                     }
                     for (int r = gp.gt; r < Z; r += gp.T) {
                         const int f = check_node(
-                            deg, km, kb, writeR,
+                            deg, km, kb, writeR, Pc, Pn,
                             [&](int p) {
                                 const int t = r + rsh[p];
                                 return rjz4[p] + 4 * (int)min((unsigned)t, (unsigned)(t - Z));
@@ -172,7 +187,7 @@ struct PairDecoder {
                     const int16_t *rs = sg.rs + i * g.dc_max;
                     for (int r = gp.gt; r < Z; r += gp.T) {
                         const int f = check_node(
-                            deg, km, kb, writeR,
+                            deg, km, kb, writeR, Pc, Pn,
                             [&](int p) {
                                 const int t = r + rs[p];
                                 return 4 * (rjz[p] + (int)min((unsigned)t, (unsigned)(t - Z)));
@@ -184,71 +199,18 @@ struct PairDecoder {
                 }
             }
         } else {
-            for (int c = gp.gt; c < g.m; c += gp.T) {
+            const int m = g.m;
+            for (int c = gp.gt; c < m; c += gp.T) {
                 const int e0 = sg.c_ptr[c];
                 const int deg = EXACT ? DC : sg.c_ptr[c + 1] - e0;
                 const int f = check_node(
-                    deg, km, kb, writeR, [&](int p) { return 4 * (int)sg.c_vn[e0 + p]; },
-                    [&](int p) { return (e0 + p) * RSZ; });
+                    deg, km, kb, writeR, Pc, Pn, [&](int p) { return 4 * (int)sg.c_vn[e0 + p]; },
+                    [&](int p) { return (p * m + c) * RSZ; });
                 u0 += f & 1;
                 u1 += f >> 1;
             }
         }
-        const int s = gp.sum(u0 | (u1 << 16));
-        return s;
-    }
-
-    // channel value L'(v) of a non-impulse node, packed for both halves
-    __device__ __forceinline__ unsigned lbase2(int dv, int Lb) const {
-        const unsigned l = (unsigned)(Lb + (int)kBeta - dv * pc.B);
-        return l | (l << 16);
-    }
-
-    // posterior pass (both halves): P' = L' + sum R'
-    __device__ __forceinline__ void vn_pass(int Lb) const {
-        const int Z = g.Z;
-        if constexpr (QC) {
-            for (int j = 0; j < g.n_b; j++) {
-                const int dv = sg.cdeg[j];
-                const unsigned l2 = lbase2(dv, Lb);
-                if (dv <= 4) {
-                    int ce[4], csh[4];
-#pragma unroll
-                    for (int t = 0; t < 4; t++)
-                        if (t < dv) {
-                            ce[t] = sg.ceoff[j * g.dv_max + t] * RSZ;
-                            csh[t] = sg.cs[j * g.dv_max + t];
-                        }
-                    for (int k = gp.gt; k < Z; k += gp.T) {
-                        unsigned acc = l2;
-#pragma unroll
-                        for (int t = 0; t < 4; t++)
-                            if (t < dv) {
-                                const int rr = k - csh[t];
-                                acc += ldR(ce[t] + RSZ * (int)min((unsigned)rr, (unsigned)(rr + Z)));
-                            }
-                        P[j * Z + k] = acc;
-                    }
-                } else {
-                    for (int k = gp.gt; k < Z; k += gp.T) {
-                        unsigned acc = l2;
-                        for (int t = 0; t < dv; t++) {
-                            const int idx = j * g.dv_max + t;
-                            const int rr = k - sg.cs[idx];
-                            acc += ldR(sg.ceoff[idx] * RSZ + RSZ * (int)min((unsigned)rr, (unsigned)(rr + Z)));
-                        }
-                        P[j * Z + k] = acc;
-                    }
-                }
-            }
-        } else {
-            for (int v = gp.gt; v < g.n; v += gp.T) {
-                const int t0 = sg.v_ptr[v], t1 = sg.v_ptr[v + 1];
-                unsigned acc = lbase2(t1 - t0, Lb);
-                for (int t = t0; t < t1; t++) acc += ldR(sg.v_edge[t] * RSZ);
-                P[v] = acc;
-            }
-        }
+        return gp.sum(u0 | (u1 << 16));
     }
 
     __device__ __forceinline__ int vdeg(int v) const {
@@ -256,34 +218,31 @@ struct PairDecoder {
         else return sg.v_ptr[v + 1] - sg.v_ptr[v];
     }
 
-    // half h of P'[v] for an impulse node: L + beta before the first check
-    // pass, else L' + the sum of its half's messages
-    __device__ __forceinline__ unsigned half_post(int v, int h, int L, bool with_msgs) const {
-        if (!with_msgs) return (unsigned)(L + (int)kBeta) & 0xFFFFu;
-        const int dv = vdeg(v);
-        unsigned acc = (unsigned)(L + (int)kBeta - dv * pc.B);
-        {
-            for (int t = 0; t < dv; t++) {
-                int e;
-                if constexpr (QC) {
-                    const int j = v / g.Z, k = v - j * g.Z;
-                    const int idx = j * g.dv_max + t;
-                    e = sg.ceoff[idx] + wrapZneg(k - sg.cs[idx], g.Z);
-                } else {
-                    e = sg.v_edge[sg.v_ptr[v] + t];
-                }
-                acc += (ldR(e * RSZ) >> (16 * h)) & 0xFFFFu;
+    // the accumulator: L'(v) = L + beta - dv B in both halves (impulse
+    // nodes are patched afterwards)
+    __device__ __forceinline__ void init_accum(unsigned *Pn, int Lb) const {
+        if constexpr (QC) {
+            const int Z = g.Z;
+            for (int j = 0; j < g.n_b; j++) {
+                const unsigned l = (unsigned)(Lb + (int)kBeta - sg.cdeg[j] * pc.B);
+                const unsigned l2 = l | (l << 16);
+                unsigned *row = Pn + j * Z;
+                for (int k = gp.gt; k < Z; k += gp.T) row[k] = l2;
+            }
+        } else {
+            for (int v = gp.gt; v < g.n; v += gp.T) {
+                const unsigned l = (unsigned)(Lb + (int)kBeta - vdeg(v) * pc.B);
+                Pn[v] = l | (l << 16);
             }
         }
-        return acc & 0xFFFFu;
     }
 
-    __device__ __forceinline__ void set_half(int v, int h, unsigned val) const {
+    __device__ __forceinline__ static void set_half(unsigned *P, int v, int h, unsigned val) {
         ((uint16_t *)P)[2 * v + h] = (uint16_t)val;
     }
 
     // x_k of half h (P < 0, i.e. bit 15 of the half clear) into a bitmask
-    __device__ __forceinline__ void save_x(int h, uint32_t *xw) const {
+    __device__ __forceinline__ void save_x(const unsigned *P, int h, uint32_t *xw) const {
         const unsigned bitpos = 15u + 16u * h;
         for (int base = 0; base < g.n; base += gp.T) {
             const int v = base + gp.gt;
@@ -294,7 +253,7 @@ struct PairDecoder {
         }
     }
 
-    __device__ __forceinline__ int any_neg(int h) const {
+    __device__ __forceinline__ int any_neg(const unsigned *P, int h) const {
         const unsigned bitpos = 15u + 16u * h;
         int neg = 0;
         for (int v = gp.gt; v < g.n; v += gp.T) neg |= !((P[v] >> bitpos) & 1u);
@@ -321,7 +280,7 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
     gp.bar = 1 + grp;
     gp.red = misc->red;
     unsigned char *Rb = slot + lay.r_off;
-    unsigned *P = (unsigned *)(slot + lay.p_off);
+    unsigned *Pbuf = (unsigned *)(slot + lay.p_off);  // [2][n]
     const int nw = (g.n + 31) >> 5;
     uint32_t *xb = (uint32_t *)(slot + lay.xa_off);  // 4 buffers of nw words: [half][cur/keep]
     const int xstride = (nw + 3) & ~3;
@@ -337,13 +296,14 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
     pc.LO2 = (kBeta - (unsigned)pc.B - (unsigned)pc.sat) * 0x00010001u;
     pc.HI2 = (kBeta - (unsigned)pc.B + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
-    PairDecoder<QC, DC, EXACT, I8> dec{g, sg, gp, dp, pc, Rb, P};
+    PairDecoder<QC, DC, EXACT, I8> dec{g, sg, gp, pc, Rb};
 
     const long long total = (long long)b.ctr->n_cand_total;
     const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
     const int Lb = clampi(dp.base_llr, -dp.sat, dp.sat);
     const int amax = (1 << dp.amp_steps) - 1;
     long long my_dec = 0, my_it = 0;
+    int pcur = 0;  // which posterior buffer holds P_k
 
     Half H[2];
 
@@ -352,8 +312,13 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
         gp.sync();
         const long long idx = b.cand_begin + misc->bcast[0];
         gp.sync();
+        h.k = 0;
+        h.ubest = 0x7fffffff;
+        h.first = 1;
+        h.cur = 0;
         if (idx >= end) {
             h.idx = -1;
+            h.nI = 0;
             return;
         }
         const int4 I4 = b.cands[idx];
@@ -362,10 +327,9 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
         h.nI = (I4.x >= 0) + (I4.y >= 0) + (I4.z >= 0) + (I4.w >= 0);
         h.lo = 0; h.hi = amax; h.st = 0; h.phase = 0;
         h.thr = -1; h.ndec = 0; h.nit = 0; h.failed = 0;
-        h.cur = 0;
         h.Limp = clampi(dp.base_llr - amax, -dp.sat, dp.sat);
     };
-    // finish candidate of half hh (records, x* to global) and fetch the next
+    // finish the candidate of half hh (records, x* to global) and fetch the next
     auto finish = [&](Half &h, int hh) {
         gp.sync();
         const long long o = h.idx - b.cand_begin;
@@ -388,11 +352,10 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
     };
     // Advance half hh past trivial decodes (impulse LLR >= 0: every hard
     // decision 0, u_0 = 0, success at iteration 0) until a decode that needs
-    // iterations is set up in h (returns true) or no candidate is left.
+    // iterations is set up (returns true) or no candidate is left.
     auto settle = [&](Half &h, int hh) {
         while (h.idx >= 0) {
             if (h.Limp < 0) return true;
-            // trivial success
             h.ndec++;
             if (h.phase == 0) {
                 finish(h, hh);  // no failure at the largest amplitude
@@ -410,33 +373,42 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
         }
         return false;
     };
-    // (re)initialize half hh of P' for a new decode
-    auto start = [&](Half &h, int hh) {
-        for (int base = 0; base < g.n; base += gp.T) {
-            const int v = base + gp.gt;
-            if (v < g.n) dec.set_half(v, hh, (unsigned)(Lb + (int)kBeta));
-        }
-        gp.sync();
-        if (gp.gt < h.nI) {
-            const int t = h.Ik(gp.gt);
-            dec.set_half(t, hh, dec.half_post(t, hh, h.Limp, false));
-        }
-        gp.sync();
+    // half hh of the current posteriors for a new decode: P = L
+    auto start_cur = [&](Half &h, int hh, unsigned *Pc) {
+        for (int v = gp.gt; v < g.n; v += gp.T) dec.set_half(Pc, v, hh, (unsigned)(Lb + (int)kBeta));
         h.k = 0;
         h.ubest = 0x7fffffff;
         h.first = 1;
     };
+    // impulse nodes: the current posteriors (new decode only) and the accumulator
+    auto patch = [&](Half &h, int hh, unsigned *Pc, unsigned *Pn, bool cur_too) {
+        if (h.idx >= 0 && gp.gt < h.nI) {
+            const int t = h.Ik(gp.gt);
+            if (cur_too) dec.set_half(Pc, t, hh, (unsigned)(h.Limp + (int)kBeta));
+            dec.set_half(Pn, t, hh, (unsigned)(h.Limp + (int)kBeta - dec.vdeg(t) * pc.B));
+        }
+    };
 
-    for (int hh = 0; hh < 2; hh++) {
-        fetch(H[hh]);
-        if (settle(H[hh], hh)) start(H[hh], hh);
+    {
+        unsigned *Pc = Pbuf, *Pn = Pbuf + g.n;
+        dec.init_accum(Pn, Lb);
+        for (int hh = 0; hh < 2; hh++) {
+            fetch(H[hh]);
+            settle(H[hh], hh);
+            start_cur(H[hh], hh, Pc);  // idle halves too: every word stays a valid decode state
+        }
+        gp.sync();
+        for (int hh = 0; hh < 2; hh++) patch(H[hh], hh, Pc, Pn, true);
+        gp.sync();
     }
 
     while (H[0].idx >= 0 || H[1].idx >= 0) {
+        unsigned *Pc = Pbuf + pcur * g.n, *Pn = Pbuf + (pcur ^ 1) * g.n;
         const unsigned km = (H[0].first ? 0xFFFF0000u : 0xFFFFFFFFu) & (H[1].first ? 0x0000FFFFu : 0xFFFFFFFFu);
         const unsigned kb = pc.B2 & ~km;
         const bool wr = (H[0].idx >= 0 && H[0].k < dp.K) || (H[1].idx >= 0 && H[1].k < dp.K);
-        const int us = dec.check_pass(km, kb, wr);
+        // u_k of both halves from P_k = Pc; Pn accumulates P_{k+1}
+        const int us = dec.check_pass(km, kb, wr, Pc, Pn);
         int restart[2] = {0, 0};
         for (int hh = 0; hh < 2; hh++) {
             Half &h = H[hh];
@@ -445,13 +417,13 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
             uint32_t *xc = xb + (2 * hh + h.cur) * xstride;
             if (h.k >= g.wstart && u < h.ubest) {
                 h.ubest = u;
-                dec.save_x(hh, xc);
+                dec.save_x(Pc, hh, xc);
             }
             if (u != 0 && h.k != dp.K) continue;
             // the decode ended at K_last = k
             const int kl = h.k;
-            if (kl < g.wstart) dec.save_x(hh, xc);
-            const bool fail = u != 0 || dec.any_neg(hh) != 0;
+            if (kl < g.wstart) dec.save_x(Pc, hh, xc);
+            const bool fail = u != 0 || dec.any_neg(Pc, hh) != 0;
             h.ndec++;
             h.nit += kl;
             if (h.phase == 0) {
@@ -483,24 +455,22 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
             }
             restart[hh] = 1;
         }
-        const bool cont0 = H[0].idx >= 0 && !restart[0], cont1 = H[1].idx >= 0 && !restart[1];
-        if (cont0 || cont1) {
-            dec.vn_pass(Lb);
-            gp.sync();
-            for (int hh = 0; hh < 2; hh++) {
-                Half &h = H[hh];
-                if (!(hh == 0 ? cont0 : cont1)) continue;
-                if (gp.gt < h.nI) {
-                    const int t = h.Ik(gp.gt);
-                    dec.set_half(t, hh, dec.half_post(t, hh, h.Limp, true));
-                }
+        // Pn (= P_{k+1}) becomes current; the old Pc becomes the next accumulator
+        gp.sync();
+        for (int hh = 0; hh < 2; hh++) {
+            Half &h = H[hh];
+            if (restart[hh]) {
+                if (settle(h, hh)) start_cur(h, hh, Pn);
+            } else if (h.idx >= 0) {
                 h.k++;
                 h.first = 0;
             }
-            gp.sync();
         }
-        for (int hh = 0; hh < 2; hh++)
-            if (restart[hh] && settle(H[hh], hh)) start(H[hh], hh);
+        dec.init_accum(Pc, Lb);
+        gp.sync();
+        for (int hh = 0; hh < 2; hh++) patch(H[hh], hh, Pn, Pc, restart[hh] != 0);
+        gp.sync();
+        pcur ^= 1;
     }
     if (gp.gt == 0) {
         atomicAdd(&b.ctr->decodes, (unsigned long long)my_dec);
