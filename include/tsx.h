@@ -198,6 +198,41 @@ TSX_API int ts_list_stats(tsx_ts_list *list, tsx_enum_stats *stats);
 
 TSX_API void free_ts_list(tsx_ts_list *list);
 
+/* ---- decoding without allocation (no counterpart in the paper) --------
+ * For callers that cannot allocate device memory -- a latency-critical host
+ * thread that must not take the driver's allocation locks, code running
+ * under another framework's memory manager that forbids outside cudaMalloc,
+ * or a process that has reserved the whole device -- this entry point runs
+ * the impulse decodes with amplitude bisection (the kernel enumerate_ts()
+ * uses) on candidate sets the caller supplies, and keeps all of its working
+ * memory in one fixed device array of TSX_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   code:      a code loaded earlier with load_code() on the current device.
+ *   params:    as for enumerate_ts(); the candidate fields are ignored.
+ *   cand_vars: device, 16-byte aligned, n_cand x 4 int32: variable nodes of
+ *              each impulse set, -1 padded at the end (1 to 4 nodes).
+ *   thr:       device, n_cand int32 out: min-sum threshold amplitude, -1 if
+ *              the decoder never failed (and -1 for the float decoder).
+ *   thr_f:     device, n_cand float out (may be NULL): float-decoder
+ *              threshold eps, -1 otherwise.
+ *   decodes, iters: device, n_cand int32 out: decodes run and iterations
+ *              executed per candidate.
+ * Returns TSX_ENOMEM, without touching the outputs, when
+ *   n_cand * (28 + 4 * ceil(n / 32)) + ~2 KB > TSX_NOALLOC_SCRATCH_BYTES,
+ * TSX_EINVAL for a malformed candidate set (checked on the device; this
+ * check waits for the stream), a misaligned pointer or a code loaded on
+ * another device.  The decode itself is enqueued on `stream` and not waited
+ * for.  The first call on each device looks up the array's device address
+ * (make that first call before any stream capture).  Every call uses the
+ * same array and finds the previous call's contents in it; the counters it
+ * relies on are reset at the start of each call, so calls that overlap on
+ * the GPU (on different streams or threads) race and must not be issued. */
+#define TSX_NOALLOC_SCRATCH_BYTES (16u << 20)
+TSX_API int decode_thresholds_noalloc(const tsx_code *code, const tsx_enum_params *params,
+                                      const int32_t *cand_vars, int64_t n_cand, int32_t *thr, float *thr_f,
+                                      int32_t *decodes, int32_t *iters, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

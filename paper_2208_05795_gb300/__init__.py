@@ -10,6 +10,7 @@ from ._tsx import (  # noqa: F401
     TsList,
     TsxError,
     code_info,
+    decode_thresholds_noalloc,
     enum_params_default,
     enumerate_ts,
     free_code,

@@ -100,6 +100,8 @@ def lib():
             L.ts_list_stats.restype = C.c_int
             L.free_ts_list.argtypes = [vp]
             L.free_ts_list.restype = None
+            L.decode_thresholds_noalloc.argtypes = [vp, C.POINTER(EnumParams), vp, C.c_int64, vp, vp, vp, vp, vp]
+            L.decode_thresholds_noalloc.restype = C.c_int
             _lib = L
     return _lib
 
@@ -260,3 +262,16 @@ def free_ts_list(lst: TsList):
     if lst.h:
         lib().free_ts_list(lst.h)
         lst.h = None
+
+
+def decode_thresholds_noalloc(code: Code, cand_vars_ptr: int, n_cand: int, thr_ptr: int, thr_f_ptr, decodes_ptr: int,
+                              iters_ptr: int, params=None, stream=None, check: bool = True, **kw) -> int:
+    """decode_thresholds_noalloc(): decodes caller-given candidate sets with
+    no device allocation; all pointers are device addresses (ints) of the
+    caller's buffers (thr_f_ptr may be None).  Returns the status."""
+    p = params if isinstance(params, EnumParams) else make_params(**(params or {}), **kw)
+    st = lib().decode_thresholds_noalloc(code.h, C.byref(p), cand_vars_ptr, int(n_cand), thr_ptr, thr_f_ptr,
+                                         decodes_ptr, iters_ptr, _stream_handle(stream))
+    if check:
+        _check(st, "decode_thresholds_noalloc")
+    return st

@@ -385,6 +385,21 @@ static int check_params(const tsx_enum_params &p) {
     return TSX_OK;
 }
 
+// accessors for the other translation units of the library
+namespace tsx {
+const DevCode *code_dev(const tsx_code *c) { return &c->d; }
+int code_num_sms(const tsx_code *c) { return c->num_sms; }
+int code_device(const tsx_code *c) { return c->device; }
+int enum_params_to_decode(const tsx_enum_params *p, DecodeParams *dp) {
+    const int st = check_params(*p);
+    if (st != TSX_OK) return st;
+    dp->decoder = p->decoder; dp->K = p->K; dp->base_llr = p->base_llr; dp->sat = p->sat;
+    dp->alpha_num = p->alpha_num; dp->alpha_shift = p->alpha_shift; dp->amp_steps = p->amp_steps;
+    dp->spa_clip = p->spa_clip; dp->spa_amax = p->spa_amax;
+    return TSX_OK;
+}
+}  // namespace tsx
+
 static long long next_pow2(long long x) {
     long long p = 1;
     while (p < x) p <<= 1;

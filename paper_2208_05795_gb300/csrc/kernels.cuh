@@ -68,6 +68,13 @@ cudaError_t launch_sieve(const DevCode &g, const EnumBuffers &b, int decoder, in
 // Whether one codeword of g fits the shared memory of a CTA.
 bool decode_fits(const DevCode &g, int decoder);
 
+// accessors of a loaded code (api.cu)
+const DevCode *code_dev(const tsx_code *c);
+int code_num_sms(const tsx_code *c);
+int code_device(const tsx_code *c);
+// validates enumeration parameters and extracts the decoder's part
+int enum_params_to_decode(const tsx_enum_params *p, DecodeParams *dp);
+
 // Compacts the hash table: assigns each stored trapping set an index,
 // writes its pool offset / count / min threshold, and rewrites the
 // candidates' slots as indices.
