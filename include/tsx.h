@@ -198,6 +198,52 @@ TSX_API int ts_list_stats(tsx_ts_list *list, tsx_enum_stats *stats);
 
 TSX_API void free_ts_list(tsx_ts_list *list);
 
+/* ---- importance-sampling FER toward a trapping set ------------------ */
+/* The weighting step the paper takes from Cole (Sec. II-III: trapping sets
+ * are weighed by importance sampling and summed into a generalized union
+ * bound; the paper gives no formula).  Definition used: BPSK over AWGN with
+ * sigma^2 = 1 / (2 R Eb/N0); the noise on the trapping-set bits is shifted
+ * by -mu; every sample is decoded by the fixed-point min-sum decoder from
+ * the all-zero codeword; FER = mean(fail * w) with
+ *   log w = sum_{v in T, ascending} (n_v mu / sigma^2 - mu^2 / (2 sigma^2))
+ * in double precision (mu = 0 is plain Monte Carlo).  Noise: Philox4x32-10
+ * with key (job_key) and counter (v / 4, sample low, sample high, 0), four
+ * uniforms u = (2 (x >> 9) + 1) 2^-24 per call, two single-precision
+ * Box-Muller pairs from IEEE-rounded series; channel LLR quantized to
+ * round-half-away(8 * 2 y / sigma^2), saturated to +-sat. */
+typedef struct {
+    double ebn0_db;        /* Eb/N0 in dB */
+    double rate;           /* code rate R; 0 = 1 - m/n */
+    double mu;             /* mean shift of the noise on the set's bits */
+    int64_t n_samples;
+    uint64_t job_key;      /* Philox key */
+    int64_t sample_begin;  /* index of the first sample (for sharding) */
+    int32_t K, sat, alpha_num, alpha_shift;  /* the min-sum decoder */
+} tsx_is_params;
+
+typedef struct {
+    double fer;            /* mean(fail * w) */
+    double var;            /* variance of that mean: (mean(w^2 fail) - fer^2) / N */
+    double sum_w, sum_w2;  /* sums of fail * w and (fail * w)^2 (fixed-order reduction) */
+    int64_t n_samples, n_fail;
+    int64_t decodes, iterations, edge_updates;
+    double ms;             /* device time (CUDA events) */
+} tsx_is_result;
+
+/* Defaults: 4 dB, R = 1 - m/n, mu = 1, 100000 samples, key 0, K = 20,
+ * sat 511, alpha 3/4. */
+TSX_API void is_params_default(tsx_is_params *p);
+
+/* Runs n_samples samples on `stream` and waits for them.  ts_vars: host,
+ * the a variable nodes of the trapping set (any order; duplicates ignored).
+ * fail_out (host, n_samples bytes) and logw_out (host, n_samples doubles)
+ * receive the per-sample failure flags and log-weights when not NULL.
+ * Errors: TSX_EINVAL (node outside the code, bad parameters),
+ * TSX_EUNSUPPORTED (degrees or saturation outside the decoder's 16-bit
+ * bounds), TSX_ENOMEM, TSX_ECUDA. */
+TSX_API int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *params,
+                            void *stream, tsx_is_result *out, uint8_t *fail_out, double *logw_out);
+
 /* ---- decoding without allocation (no counterpart in the paper) --------
  * For callers that cannot allocate device memory -- a latency-critical host
  * thread that must not take the driver's allocation locks, code running

@@ -48,6 +48,11 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+class _IsParams(C.Structure):
+    _fields_ = [("ebn0_db", C.c_double), ("rate", C.c_double), ("mu", C.c_double), ("job", C.c_uint64),
+                ("K", C.c_int), ("sat", C.c_int), ("alpha_num", C.c_int), ("alpha_shift", C.c_int)]
+
+
 class _Params(C.Structure):
     _fields_ = [("decoder", C.c_int), ("K", C.c_int), ("base_llr", C.c_int), ("sat", C.c_int),
                 ("alpha_num", C.c_int), ("alpha_shift", C.c_int), ("amp_steps", C.c_int),
@@ -109,8 +114,42 @@ def lib():
             L.og_tanhf.restype = C.c_float
             L.og_atanhf.argtypes = [C.c_float]
             L.og_atanhf.restype = C.c_float
+            U32P = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
+            F64P = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+            L.og_philox4x32_10.argtypes = [U32P, U32P, U32P]
+            L.og_logf.argtypes = [C.c_float]
+            L.og_logf.restype = C.c_float
+            L.og_sincos2pi.argtypes = [C.c_float, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+            L.og_normals4.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, F32P]
+            L.og_is_samples.argtypes = [C.c_void_p, I32P, C.c_int, C.POINTER(_IsParams), C.c_uint64, C.c_int,
+                                        U8P, F64P]
             _lib = L
     return _lib
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 (Salmon et al., SC'11) of a 4-word counter and 2-word key."""
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib().og_philox4x32_10(c, k, out)
+    return out
+
+
+def logf(x: float) -> float:
+    return float(lib().og_logf(float(x)))
+
+
+def sincos2pi(t: float):
+    s, c = C.c_float(), C.c_float()
+    lib().og_sincos2pi(float(t), C.byref(s), C.byref(c))
+    return s.value, c.value
+
+
+def normals4(job: int, sample: int, quad: int) -> np.ndarray:
+    g = np.zeros(4, dtype=np.float32)
+    lib().og_normals4(int(job), int(sample), int(quad), g)
+    return g
 
 
 def tanhf(x: float) -> float:
@@ -264,6 +303,18 @@ class Graph:
         T = np.zeros(self.n, dtype=np.uint8)
         which = lib().og_extract(self.h, xs, Ia, Ia.size, T)
         return which, set(np.flatnonzero(T).tolist())
+
+    # --- importance-sampling FER ----------------------------------------
+    def is_samples(self, T, *, ebn0_db, rate=None, mu=1.0, job=0, s0=0, n=1000, K=20, sat=511,
+                   alpha_num=3, alpha_shift=2):
+        """Per-sample failure flags and log-weights of the mean-shift IS estimator."""
+        Ta = np.ascontiguousarray(np.sort(np.asarray(list(T), dtype=np.int32)))
+        r = (1.0 - self.m / self.n) if rate is None else rate
+        p = _IsParams(float(ebn0_db), float(r), float(mu), int(job), K, sat, alpha_num, alpha_shift)
+        fail = np.zeros(n, dtype=np.uint8)
+        logw = np.zeros(n, dtype=np.float64)
+        lib().og_is_samples(self.h, Ta, Ta.size, C.byref(p), int(s0), int(n), fail, logw)
+        return fail, logw
 
     # --- the whole method -----------------------------------------------
     def enumerate(self, cands=None, *, decoder="nms", K=20, base_llr=16, sat=511, alpha_num=3,

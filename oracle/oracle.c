@@ -843,3 +843,170 @@ void og_res_free(og_result *R) {
     free(R->list); free(R->thr); free(R->thr_f); free(R->ts); free(R->which);
     free(R->decodes); free(R->iters); free(R);
 }
+
+/* ------------------------------------------------------------------ */
+/* Importance-sampling FER toward a trapping set                        */
+/* ------------------------------------------------------------------ */
+/* Sec. II-III name Cole's weighting of trapping sets by importance
+ * sampling without a formula; the definition used here is mean-shift
+ * importance sampling of BPSK over AWGN toward the set T:
+ *   sigma^2 = 1 / (2 R Eb/N0); noise n_v = sigma g_v, g_v ~ N(0,1);
+ *   y_v = 1 + n_v - mu [v in T]; channel LLR 2 y_v / sigma^2, quantized as
+ *   round-half-away(8 * LLR) saturated to +-sat; decoded by the min-sum
+ *   decoder from the all-zero codeword; fail = decoder failure;
+ *   log w = sum_{v in T, ascending} (n_v mu / sigma^2 - mu^2 / (2 sigma^2))
+ *   (the likelihood ratio of the shifted Gaussian, in double precision);
+ *   FER = mean(fail * w).
+ * Noise: g_v from Philox4x32-10 (Salmon et al., SC'11) with key (job low,
+ * job high) and counter (v / 4, sample low, sample high, 0); its four
+ * outputs x_0..x_3 become uniforms u = (2 (x >> 9) + 1) 2^-24 and two
+ * Box-Muller pairs (Box and Muller 1958) (u_0,u_1) -> g_{4q}, g_{4q+1} and
+ * (u_2,u_3) -> g_{4q+2}, g_{4q+3}: r = sqrt(-2 ln u_a), g = r cos(2 pi u_b),
+ * g' = r sin(2 pi u_b), in single precision with IEEE-rounded operations:
+ * ln by frexp and the atanh series of log, sin/cos of 2 pi u by quadrant
+ * reduction and their Taylor series on [0, pi/4]. */
+
+static void og_philox(uint32_t c[4], uint32_t k0, uint32_t k1) {
+    for (int r = 0; r < 10; r++) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c[0], p1 = (uint64_t)0xCD9E8D57u * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0, hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+void og_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    og_philox(c, key[0], key[1]);
+    memcpy(out, c, sizeof(c));
+}
+
+float og_logf(float u) {
+    int e;
+    float m = frexpf(u, &e);
+    if (m < OG_SQRT_HALF) { m = m + m; e = e - 1; }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float s2 = s * s;
+    float q = 1.0f / 13.0f;
+    q = q * s2 + 1.0f / 11.0f;
+    q = q * s2 + 1.0f / 9.0f;
+    q = q * s2 + 1.0f / 7.0f;
+    q = q * s2 + 1.0f / 5.0f;
+    q = q * s2 + 1.0f / 3.0f;
+    q = q * s2 + 1.0f;
+    return (float)e * OG_LN2 + (s + s) * q;
+}
+
+static float og_sin_poly(float a) {  /* a in [0, pi/4] */
+    float a2 = a * a;
+    float p = 1.0f / 362880.0f;
+    p = p * a2 - 1.0f / 5040.0f;
+    p = p * a2 + 1.0f / 120.0f;
+    p = p * a2 - 1.0f / 6.0f;
+    p = p * a2 + 1.0f;
+    return p * a;
+}
+static float og_cos_poly(float a) {
+    float a2 = a * a;
+    float p = -1.0f / 3628800.0f;
+    p = p * a2 + 1.0f / 40320.0f;
+    p = p * a2 - 1.0f / 720.0f;
+    p = p * a2 + 1.0f / 24.0f;
+    p = p * a2 - 0.5f;
+    p = p * a2 + 1.0f;
+    return p;
+}
+
+/* sin and cos of 2 pi t, t in [0, 1) */
+void og_sincos2pi(float t, float *s, float *c) {
+    float t4 = t * 4.0f;
+    float kf = floorf(t4);
+    int k = (int)kf;
+    float f = t4 - kf; /* exact */
+    float sa, ca;
+    const float HALF_PI = 1.57079632679489662f;
+    if (f <= 0.5f) {
+        float a = f * HALF_PI;
+        sa = og_sin_poly(a); ca = og_cos_poly(a);
+    } else {
+        float a = (1.0f - f) * HALF_PI;
+        sa = og_cos_poly(a); ca = og_sin_poly(a);
+    }
+    switch (k & 3) {
+        case 0: *s = sa; *c = ca; break;
+        case 1: *s = ca; *c = -sa; break;
+        case 2: *s = -sa; *c = -ca; break;
+        default: *s = -ca; *c = sa; break;
+    }
+}
+
+static float og_uniform(uint32_t x) { return (float)(2u * (x >> 9) + 1u) * 0x1p-24f; }
+
+/* the four normals of VN quad q of sample s */
+void og_normals4(uint64_t job, uint64_t s, uint32_t q, float g[4]) {
+    uint32_t c[4] = {q, (uint32_t)s, (uint32_t)(s >> 32), 0u};
+    og_philox(c, (uint32_t)job, (uint32_t)(job >> 32));
+    for (int pr = 0; pr < 2; pr++) {
+        float ua = og_uniform(c[2 * pr]), ub = og_uniform(c[2 * pr + 1]);
+        float r = sqrtf(-2.0f * og_logf(ua));
+        float sn, cs;
+        og_sincos2pi(ub, &sn, &cs);
+        g[2 * pr] = r * cs;
+        g[2 * pr + 1] = r * sn;
+    }
+}
+
+typedef struct {
+    double ebn0_db, rate, mu;
+    uint64_t job;
+    int K, sat, alpha_num, alpha_shift;
+} og_is_params;
+
+/* sigma^2, the float constants and the log-weight coefficients */
+static void og_is_consts(const og_is_params *p, float *sigf, float *muf, float *cq, double *A, double *Bc) {
+    double ebn0 = pow(10.0, p->ebn0_db / 10.0);
+    double s2 = 1.0 / (2.0 * p->rate * ebn0);
+    *sigf = (float)sqrt(s2);
+    *muf = (float)p->mu;
+    *cq = (float)(16.0 / s2);
+    *A = p->mu / s2;
+    *Bc = p->mu * p->mu / (2.0 * s2);
+}
+
+/* Samples [s0, s0 + ns): fail flags and log-weights. */
+void og_is_samples(const og_graph *g, const int *T, int a, const og_is_params *p, uint64_t s0, int ns,
+                   unsigned char *fail, double *logw) {
+    float sigf, muf, cq;
+    double A, Bc;
+    og_is_consts(p, &sigf, &muf, &cq, &A, &Bc);
+    int *L = (int *)malloc(sizeof(int) * g->n);
+    unsigned char *inT = (unsigned char *)calloc(g->n, 1), *xb = (unsigned char *)malloc(g->n);
+    float *nv = (float *)malloc(sizeof(float) * g->n);
+    for (int t = 0; t < a; t++) inT[T[t]] = 1;
+    for (int i = 0; i < ns; i++) {
+        uint64_t s = s0 + (uint64_t)i;
+        for (int q = 0; 4 * q < g->n; q++) {
+            float gq[4];
+            og_normals4(p->job, s, (uint32_t)q, gq);
+            for (int j = 0; j < 4 && 4 * q + j < g->n; j++) {
+                int v = 4 * q + j;
+                float n = sigf * gq[j];
+                float y = 1.0f + n;
+                if (inT[v]) y = y - muf;
+                float lq = roundf(y * cq);
+                int li = lq > (float)p->sat ? p->sat : lq < -(float)p->sat ? -p->sat : (int)lq;
+                L[v] = li;
+                nv[v] = n;
+            }
+        }
+        int kl;
+        fail[i] = (unsigned char)og_decode_nms(g, L, p->K, p->sat, p->alpha_num, p->alpha_shift, 1, xb, &kl,
+                                              NULL, NULL);
+        double lw = 0.0;
+        for (int v = 0; v < g->n; v++)
+            if (inT[v]) lw = lw + ((double)nv[v] * A - Bc);
+        logw[i] = lw;
+    }
+    free(L); free(inT); free(xb); free(nv);
+}

@@ -15,6 +15,8 @@ from ._tsx import (  # noqa: F401
     enumerate_ts,
     free_code,
     free_ts_list,
+    is_fer_estimate,
+    is_params_default,
     lib,
     load_code,
     make_params,

@@ -61,6 +61,18 @@ class EnumStats(C.Structure):
                 ("ms_decode", C.c_double), ("ms_sieve", C.c_double)]
 
 
+class IsParams(C.Structure):
+    _fields_ = [("ebn0_db", C.c_double), ("rate", C.c_double), ("mu", C.c_double), ("n_samples", C.c_int64),
+                ("job_key", C.c_uint64), ("sample_begin", C.c_int64), ("K", C.c_int32), ("sat", C.c_int32),
+                ("alpha_num", C.c_int32), ("alpha_shift", C.c_int32)]
+
+
+class IsResult(C.Structure):
+    _fields_ = [("fer", C.c_double), ("var", C.c_double), ("sum_w", C.c_double), ("sum_w2", C.c_double),
+                ("n_samples", C.c_int64), ("n_fail", C.c_int64), ("decodes", C.c_int64),
+                ("iterations", C.c_int64), ("edge_updates", C.c_int64), ("ms", C.c_double)]
+
+
 class TsView(C.Structure):
     _fields_ = [("stats", EnumStats), ("n_ts", C.c_int64), ("a", I32), ("b", I32), ("orbit", I32),
                 ("count", I32), ("thr", I32), ("flags", I32), ("thr_f", F32), ("var_off", I64),
@@ -100,6 +112,10 @@ def lib():
             L.ts_list_stats.restype = C.c_int
             L.free_ts_list.argtypes = [vp]
             L.free_ts_list.restype = None
+            L.is_params_default.argtypes = [C.POINTER(IsParams)]
+            L.is_params_default.restype = None
+            L.is_fer_estimate.argtypes = [vp, vp, C.c_int32, C.POINTER(IsParams), vp, C.POINTER(IsResult), vp, vp]
+            L.is_fer_estimate.restype = C.c_int
             L.decode_thresholds_noalloc.argtypes = [vp, C.POINTER(EnumParams), vp, C.c_int64, vp, vp, vp, vp, vp]
             L.decode_thresholds_noalloc.restype = C.c_int
             _lib = L
@@ -262,6 +278,35 @@ def free_ts_list(lst: TsList):
     if lst.h:
         lib().free_ts_list(lst.h)
         lst.h = None
+
+
+def is_params_default() -> IsParams:
+    p = IsParams()
+    lib().is_params_default(C.byref(p))
+    return p
+
+
+def is_fer_estimate(code: Code, ts_vars, stream=None, record: bool = False, **kw) -> dict:
+    """is_fer_estimate(): importance-sampling FER toward the trapping set
+    ts_vars.  Keyword arguments set tsx_is_params fields.  With record, the
+    per-sample failure flags and log-weights are returned too."""
+    p = is_params_default()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    T = _i32(ts_vars)
+    r = IsResult()
+    n = int(p.n_samples)
+    fail = np.zeros(n, dtype=np.uint8) if record else None
+    logw = np.zeros(n, dtype=np.float64) if record else None
+    _check(lib().is_fer_estimate(code.h, T.ctypes.data_as(C.c_void_p), T.size, C.byref(p), _stream_handle(stream),
+                                 C.byref(r), fail.ctypes.data_as(C.c_void_p) if record else None,
+                                 logw.ctypes.data_as(C.c_void_p) if record else None), "is_fer_estimate")
+    out = {k: getattr(r, k) for k, _ in IsResult._fields_}
+    if record:
+        out["fail"], out["logw"] = fail, logw
+    return out
 
 
 def decode_thresholds_noalloc(code: Code, cand_vars_ptr: int, n_cand: int, thr_ptr: int, thr_f_ptr, decodes_ptr: int,

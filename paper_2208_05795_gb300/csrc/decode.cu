@@ -16,7 +16,7 @@ cudaError_t launch_sieve_kernel(const DevCode &, const EnumBuffers &, const Laun
 
 namespace {
 
-enum { kLayScalar = 0, kLayPair = 1, kLaySieve = 2 };
+enum { kLayScalar = 0, kLayPair = 1, kLaySieve = 2, kLayIs = 3 };
 
 int msg_bytes(int decoder) { return decoder == TSX_DEC_NMS_I8 ? 1 : (decoder == TSX_DEC_SPA_F32 ? 4 : 2); }
 int post_bytes(int decoder) { return decoder == TSX_DEC_SPA_F32 ? 4 : 2; }
@@ -39,6 +39,11 @@ SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
         L.r_off = x; x += al16(nmsg * rsz);
         L.p_off = x; x += al16(2 * g.n * 4);  // current and accumulating posteriors
         L.xa_off = x; x += al16(4 * xstride * 4);
+        L.xb_off = L.xa_off;
+    } else if (kind == kLayIs) {
+        L.r_off = x; x += al16(nmsg * 4);
+        L.p_off = x; x += al16(3 * g.n * 4);  // two posterior buffers and the channel values
+        L.xa_off = x; x += al16(nw * 4);      // bitmask of the trapping set
         L.xb_off = L.xa_off;
     } else {
         int rbytes = 4 * g.m;
@@ -121,6 +126,11 @@ cudaError_t launch_sieve(const DevCode &g, const EnumBuffers &b, int decoder, in
     LaunchShape sh;
     if (!plan(g, decoder, kLaySieve, 1, 0, 0, num_sms, &sh)) return cudaErrorInvalidConfiguration;
     return launch_sieve_kernel(g, b, sh, decoder == TSX_DEC_SPA_F32 ? 1 : 0, st);
+}
+
+bool plan_is_shape(const DevCode &g, const DecodeParams &dp, LaunchShape *sh, int num_sms) {
+    if (!pair_ok(g, dp)) return false;
+    return plan(g, TSX_DEC_NMS_I16, kLayIs, 0, 0, 0, num_sms, sh);
 }
 
 bool decode_fits(const DevCode &g, int decoder) {

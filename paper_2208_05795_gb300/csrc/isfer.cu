@@ -1,0 +1,456 @@
+// isfer.cu -- importance-sampling FER toward a trapping set (the weighting
+// step the paper takes from Cole, Sec. II-III): mean-shift importance
+// sampling of BPSK over AWGN, with the noise on the set's bits shifted by
+// -mu, every sample decoded by the fixed-point min-sum decoder, and
+//   FER = mean over samples of fail * w,
+//   log w = sum_{v in T, ascending} (n_v mu / sigma^2 - mu^2 / (2 sigma^2)).
+// Noise: Philox4x32-10 (Salmon et al., SC'11) keyed by the job, counter
+// (v / 4, sample low, sample high, 0); uniforms u = (2 (x >> 9) + 1) 2^-24;
+// Box-Muller pairs in single precision with IEEE-rounded operations only
+// (log by frexp and the atanh series; sin/cos of 2 pi u by quadrant
+// reduction and Taylor series on [0, pi/4]); channel LLR quantized as
+// round-half-away(8 * 2 y / sigma^2) saturated to +-sat.  Log-weights in
+// double precision; the sums are reduced in a fixed order.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "decode_pair.cuh"
+
+namespace tsx {
+namespace {
+
+// ---------------------------------------------------------------------------
+// noise
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4x32_10(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t k0,
+                                              uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+}
+
+__device__ __forceinline__ float uniform24(uint32_t x) { return hmul((float)(2u * (x >> 9) + 1u), 0x1p-24f); }
+
+__device__ __forceinline__ float series_logf(float u) {
+    int e;
+    float m = frexpf(u, &e);
+    if (m < 0x1.6a09e6p-1f) {
+        m = hadd(m, m);
+        e = e - 1;
+    }
+    const float s = hdiv(hsub(m, 1.0f), hadd(m, 1.0f));
+    const float s2 = hmul(s, s);
+    float q = 0x1.3b13b2p-4f;  // 1/13
+    q = hadd(hmul(q, s2), 0x1.745d18p-4f);
+    q = hadd(hmul(q, s2), 0x1.c71c72p-4f);
+    q = hadd(hmul(q, s2), 0x1.24924ap-3f);
+    q = hadd(hmul(q, s2), 0x1.99999ap-3f);
+    q = hadd(hmul(q, s2), 0x1.555556p-2f);
+    q = hadd(hmul(q, s2), 1.0f);
+    return hadd(hmul((float)e, 0x1.62e43p-1f), hmul(hadd(s, s), q));
+}
+
+__device__ __forceinline__ float sin_poly(float a) {
+    const float a2 = hmul(a, a);
+    float p = 0x1.71de3ap-19f;                  // 1/9!
+    p = hsub(hmul(p, a2), 0x1.a01a02p-13f);     // 1/7!
+    p = hadd(hmul(p, a2), 0x1.111112p-7f);      // 1/5!
+    p = hsub(hmul(p, a2), 0x1.555556p-3f);      // 1/3!
+    p = hadd(hmul(p, a2), 1.0f);
+    return hmul(p, a);
+}
+__device__ __forceinline__ float cos_poly(float a) {
+    const float a2 = hmul(a, a);
+    float p = -0x1.27e4fcp-22f;                 // -1/10!
+    p = hadd(hmul(p, a2), 0x1.a01a02p-16f);     // 1/8!
+    p = hsub(hmul(p, a2), 0x1.6c16c2p-10f);     // 1/6!
+    p = hadd(hmul(p, a2), 0x1.555556p-5f);      // 1/4!
+    p = hsub(hmul(p, a2), 0.5f);
+    p = hadd(hmul(p, a2), 1.0f);
+    return p;
+}
+__device__ __forceinline__ void sincos2pi(float t, float &s, float &c) {
+    const float t4 = hmul(t, 4.0f);
+    const float kf = floorf(t4);
+    const int k = (int)kf;
+    const float f = hsub(t4, kf);
+    const float HALF_PI = 0x1.921fb6p+0f;
+    float sa, ca;
+    if (f <= 0.5f) {
+        const float a = hmul(f, HALF_PI);
+        sa = sin_poly(a);
+        ca = cos_poly(a);
+    } else {
+        const float a = hmul(hsub(1.0f, f), HALF_PI);
+        sa = cos_poly(a);
+        ca = sin_poly(a);
+    }
+    switch (k & 3) {
+        case 0: s = sa; c = ca; break;
+        case 1: s = ca; c = -sa; break;
+        case 2: s = -sa; c = -ca; break;
+        default: s = -ca; c = sa; break;
+    }
+}
+
+__device__ __forceinline__ void normals4(unsigned long long job, unsigned long long s, uint32_t q, float g[4]) {
+    uint32_t c0 = q, c1 = (uint32_t)s, c2 = (uint32_t)(s >> 32), c3 = 0u;
+    philox4x32_10(c0, c1, c2, c3, (uint32_t)job, (uint32_t)(job >> 32));
+    const uint32_t x[4] = {c0, c1, c2, c3};
+#pragma unroll
+    for (int pr = 0; pr < 2; pr++) {
+        const float ua = uniform24(x[2 * pr]), ub = uniform24(x[2 * pr + 1]);
+        const float r = __fsqrt_rn(hmul(-2.0f, series_logf(ua)));
+        float sn, cs;
+        sincos2pi(ub, sn, cs);
+        g[2 * pr] = hmul(r, cs);
+        g[2 * pr + 1] = hmul(r, sn);
+    }
+}
+
+struct IsArgs {
+    unsigned long long job, s0;
+    long long nsamp;
+    float sigf, muf, cq;
+    double A, Bc;
+    const int *T;
+    int a;
+    double *wfail;            // [nsamp] fail * w
+    unsigned char *fail_out;  // [nsamp] or null
+    double *logw_out;         // [nsamp] or null
+    Counters *ctr;
+};
+
+// ---------------------------------------------------------------------------
+// the sampling kernel: two samples per lane, as the enumeration decoder
+// ---------------------------------------------------------------------------
+template <bool QC, int DC, bool EXACT>
+__global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsArgs ia, SlotLayout lay, int G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SGraph sg = load_tables(g, smem);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = warp / G;
+    unsigned char *slot = smem + lay.tables_bytes + grp * lay.slot_bytes;
+    Misc *misc = (Misc *)(slot + lay.misc_off);
+    Grp gp;
+    gp.G = G;
+    gp.T = 32 * G;
+    gp.gw = warp - grp * G;
+    gp.gt = gp.gw * 32 + lane;
+    gp.lane = lane;
+    gp.bar = 1 + grp;
+    gp.red = misc->red;
+    unsigned char *Rb = slot + lay.r_off;
+    unsigned *Pbuf = (unsigned *)(slot + lay.p_off);  // [2][n]
+    unsigned *L2 = Pbuf + 2 * g.n;                    // accumulator start values, both halves
+    uint32_t *Tm = (uint32_t *)(slot + lay.xa_off);   // bitmask of T
+    const int nw = (g.n + 31) >> 5;
+
+    PairConst pc;
+    pc.B = 1024;
+    pc.sat = dp.sat;
+    pc.an = dp.alpha_num;
+    pc.as = dp.alpha_shift;
+    pc.B2 = (unsigned)pc.B * 0x00010001u;
+    pc.BETA2 = kBeta * 0x00010001u;
+    pc.BS2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
+    pc.LO2 = (kBeta - (unsigned)pc.B - (unsigned)pc.sat) * 0x00010001u;
+    pc.HI2 = (kBeta - (unsigned)pc.B + (unsigned)pc.sat) * 0x00010001u;
+    pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
+    PairDecoder<QC, DC, EXACT, false> dec{g, sg, gp, pc, Rb};
+
+    for (int w = gp.gt; w < nw; w += gp.T) Tm[w] = 0u;
+    gp.sync();
+    for (int t = gp.gt; t < ia.a; t += gp.T) atomicOr(&Tm[ia.T[t] >> 5], 1u << (ia.T[t] & 31));
+    gp.sync();
+
+    long long my_dec = 0, my_it = 0;
+    long long sidx[2];
+    int k[2], first[2];
+    int pcur = 0;
+
+    auto fetch = [&](int hh) {
+        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(&ia.ctr->next_cand, 1ull);
+        gp.sync();
+        const long long i = misc->bcast[0];
+        gp.sync();
+        sidx[hh] = i < ia.nsamp ? i : -1;
+        k[hh] = 0;
+        first[hh] = 1;
+    };
+    // channel values of sample sidx[hh] into half hh of L2 (accumulator
+    // start) and of the current posteriors (P = L); an idle half gets L = 0
+    auto generate = [&](int hh, unsigned *Pc) {
+        const unsigned long long s = ia.s0 + (unsigned long long)(sidx[hh] < 0 ? 0 : sidx[hh]);
+        for (int q = gp.gt; 4 * q < g.n; q += gp.T) {
+            float gq[4];
+            if (sidx[hh] >= 0) normals4(ia.job, s, (uint32_t)q, gq);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int v = 4 * q + j;
+                if (v >= g.n) break;
+                int L = 0;
+                if (sidx[hh] >= 0) {
+                    const float n = hmul(ia.sigf, gq[j]);
+                    float y = hadd(1.0f, n);
+                    if ((Tm[v >> 5] >> (v & 31)) & 1u) y = hsub(y, ia.muf);
+                    const float lq = roundf(hmul(y, ia.cq));
+                    L = lq > (float)dp.sat ? dp.sat : (lq < -(float)dp.sat ? -dp.sat : (int)lq);
+                }
+                dec.set_half(L2, v, hh, (unsigned)(L + (int)kBeta - dec.vdeg(v) * pc.B));
+                dec.set_half(Pc, v, hh, (unsigned)(L + (int)kBeta));
+            }
+        }
+    };
+
+    {
+        unsigned *Pc = Pbuf;
+        for (int hh = 0; hh < 2; hh++) {
+            fetch(hh);
+            generate(hh, Pc);
+        }
+        gp.sync();
+    }
+    while (sidx[0] >= 0 || sidx[1] >= 0) {
+        unsigned *Pc = Pbuf + pcur * g.n, *Pn = Pbuf + (pcur ^ 1) * g.n;
+        for (int v = gp.gt; v < g.n; v += gp.T) Pn[v] = L2[v];
+        gp.sync();
+        const unsigned km = (first[0] ? 0xFFFF0000u : 0xFFFFFFFFu) & (first[1] ? 0x0000FFFFu : 0xFFFFFFFFu);
+        const unsigned kb = pc.B2 & ~km;
+        const bool wr = (sidx[0] >= 0 && k[0] < dp.K) || (sidx[1] >= 0 && k[1] < dp.K);
+        const int us = dec.check_pass(km, kb, wr, Pc, Pn);
+        int restart[2] = {0, 0};
+        for (int hh = 0; hh < 2; hh++) {
+            if (sidx[hh] < 0) continue;
+            const int u = hh == 0 ? (us & 0xFFFF) : (us >> 16);
+            if (u != 0 && k[hh] != dp.K) continue;
+            const bool fail = u != 0 || dec.any_neg(Pc, hh) != 0;
+            if (gp.gt == 0) {
+                const unsigned long long s = ia.s0 + (unsigned long long)sidx[hh];
+                double lw = 0.0;
+                for (int t = 0; t < ia.a; t++) {
+                    const int v = ia.T[t];
+                    float gq[4];
+                    normals4(ia.job, s, (uint32_t)(v >> 2), gq);
+                    const double n = (double)hmul(ia.sigf, gq[v & 3]);
+                    lw = __dadd_rn(lw, __dsub_rn(__dmul_rn(n, ia.A), ia.Bc));
+                }
+                ia.wfail[sidx[hh]] = fail ? exp(lw) : 0.0;
+                if (fail) atomicAdd(&ia.ctr->n_fail, 1ull);
+                if (ia.fail_out) ia.fail_out[sidx[hh]] = fail ? 1 : 0;
+                if (ia.logw_out) ia.logw_out[sidx[hh]] = lw;
+            }
+            my_dec++;
+            my_it += k[hh];
+            restart[hh] = 1;
+        }
+        gp.sync();
+        for (int hh = 0; hh < 2; hh++) {
+            if (restart[hh]) {
+                fetch(hh);
+                if (sidx[hh] >= 0) generate(hh, Pn);
+            } else if (sidx[hh] >= 0) {
+                k[hh]++;
+                first[hh] = 0;
+            }
+        }
+        gp.sync();
+        pcur ^= 1;
+    }
+    if (gp.gt == 0) {
+        atomicAdd(&ia.ctr->decodes, (unsigned long long)my_dec);
+        atomicAdd(&ia.ctr->iterations, (unsigned long long)my_it);
+        atomicAdd(&ia.ctr->edge_updates, (unsigned long long)my_it * (unsigned long long)g.E);
+    }
+}
+
+// fixed-order reduction: per block, 4096 consecutive samples
+constexpr int kRedBlock = 1024, kRedChunk = 4096;
+__global__ void __launch_bounds__(kRedBlock) reduce_kernel(const double *w, long long n, double *part) {
+    __shared__ double s1[kRedBlock], s2[kRedBlock];
+    const long long base = (long long)blockIdx.x * kRedChunk;
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < kRedChunk / kRedBlock; j++) {
+        const long long i = base + (long long)threadIdx.x * (kRedChunk / kRedBlock) + j;
+        const double x = i < n ? w[i] : 0.0;
+        a = __dadd_rn(a, x);
+        b = __dadd_rn(b, __dmul_rn(x, x));
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int h = kRedBlock / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            s1[threadIdx.x] = __dadd_rn(s1[threadIdx.x], s1[threadIdx.x + h]);
+            s2[threadIdx.x] = __dadd_rn(s2[threadIdx.x], s2[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = s1[0];
+        part[2 * blockIdx.x + 1] = s2[0];
+    }
+}
+__global__ void finish_kernel(const double *part, int nb, double *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < nb; i++) {
+        a = __dadd_rn(a, part[2 * i]);
+        b = __dadd_rn(b, part[2 * i + 1]);
+    }
+    out[0] = a;
+    out[1] = b;
+}
+
+}  // namespace
+}  // namespace tsx
+
+using namespace tsx;
+
+extern "C" void is_params_default(tsx_is_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->ebn0_db = 4.0;
+    p->rate = 0.0;
+    p->mu = 1.0;
+    p->n_samples = 100000;
+    p->job_key = 0;
+    p->sample_begin = 0;
+    p->K = 20;
+    p->sat = 511;
+    p->alpha_num = 3;
+    p->alpha_shift = 2;
+}
+
+extern "C" int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p,
+                               void *stream, tsx_is_result *out, uint8_t *fail_out, double *logw_out) {
+    if (!code || !p || !out || a < 0 || (a > 0 && !ts_vars)) return TSX_EINVAL;
+    if (p->n_samples < 0 || p->sample_begin < 0 || p->K < 0 || p->K > 100000) return TSX_EINVAL;
+    if (p->sat < 1 || p->sat > 8191 || p->alpha_shift < 0 || p->alpha_shift > 15 || p->alpha_num < 1 ||
+        p->alpha_num > (1 << p->alpha_shift))
+        return TSX_EINVAL;
+    const DevCode &g = *code_dev(code);
+    for (int t = 0; t < a; t++)
+        if (ts_vars[t] < 0 || ts_vars[t] >= g.n) return TSX_EINVAL;
+    const double rate = p->rate > 0.0 ? p->rate : 1.0 - (double)g.m / (double)g.n;
+    if (!(rate > 0.0) || !(p->ebn0_db > -100.0 && p->ebn0_db < 100.0)) return TSX_EINVAL;
+    DecodeParams dp{};
+    dp.decoder = TSX_DEC_NMS_I16;
+    dp.K = p->K;
+    dp.sat = p->sat;
+    dp.alpha_num = p->alpha_num;
+    dp.alpha_shift = p->alpha_shift;
+    dp.base_llr = 1;
+    LaunchShape sh;
+    if (!plan_is_shape(g, dp, &sh, code_num_sms(code))) return TSX_EUNSUPPORTED;
+    memset(out, 0, sizeof(*out));
+    const long long N = p->n_samples;
+    out->n_samples = N;
+    if (N == 0) return TSX_OK;
+
+    // sigma^2 = 1 / (2 R Eb/N0); float constants and log-weight coefficients
+    const double ebn0 = pow(10.0, p->ebn0_db / 10.0);
+    const double s2 = 1.0 / (2.0 * rate * ebn0);
+    IsArgs ia{};
+    ia.job = p->job_key;
+    ia.s0 = (unsigned long long)p->sample_begin;
+    ia.nsamp = N;
+    ia.sigf = (float)sqrt(s2);
+    ia.muf = (float)p->mu;
+    ia.cq = (float)(16.0 / s2);
+    ia.A = p->mu / s2;
+    ia.Bc = p->mu * p->mu / (2.0 * s2);
+    ia.a = a;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<int> Ts(ts_vars, ts_vars + a);
+    std::sort(Ts.begin(), Ts.end());
+    Ts.erase(std::unique(Ts.begin(), Ts.end()), Ts.end());
+    a = (int32_t)Ts.size();
+    ia.a = a;
+    const int nb = (int)((N + kRedChunk - 1) / kRedChunk);
+    void *blk = nullptr;
+    const size_t off_T = 0, off_w = 256 + ((size_t)a * 4 + 255) / 256 * 256;
+    const size_t off_f = off_w + ((size_t)N * 8 + 255) / 256 * 256;
+    const size_t off_l = off_f + ((size_t)N + 255) / 256 * 256;
+    const size_t off_p = off_l + ((size_t)N * 8 + 255) / 256 * 256;
+    const size_t off_o = off_p + ((size_t)nb * 16 + 255) / 256 * 256;
+    const size_t off_c = off_o + 256;
+    const size_t total = off_c + 256;
+    if (cudaMallocAsync(&blk, total, s) != cudaSuccess) return TSX_ENOMEM;
+    unsigned char *B = (unsigned char *)blk;
+    ia.T = (const int *)(B + off_T);
+    ia.wfail = (double *)(B + off_w);
+    ia.fail_out = (unsigned char *)(B + off_f);
+    ia.logw_out = (double *)(B + off_l);
+    ia.ctr = (Counters *)(B + off_c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int st = TSX_OK;
+    Counters c{};
+    double sums[2] = {0.0, 0.0};
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = TSX_ECUDA;
+    if (st == TSX_OK && a > 0 &&
+        cudaMemcpyAsync((void *)ia.T, Ts.data(), sizeof(int) * a, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = TSX_ECUDA;
+    if (st == TSX_OK && cudaMemsetAsync(ia.ctr, 0, sizeof(Counters), s) != cudaSuccess) st = TSX_ECUDA;
+    if (st == TSX_OK && cudaEventRecord(e0, s) != cudaSuccess) st = TSX_ECUDA;
+    if (st == TSX_OK) {
+        const bool qc = g.kind == TSX_CODE_QC;
+        const bool reg6 = g.dc_min == 6 && g.dc_max == 6;
+        cudaError_t e;
+        if (reg6)
+            e = qc ? launch_persistent(is_kernel<true, 6, true>, sh, s, g, dp, ia, sh.lay, sh.G)
+                   : launch_persistent(is_kernel<false, 6, true>, sh, s, g, dp, ia, sh.lay, sh.G);
+        else if (g.dc_max <= 8)
+            e = qc ? launch_persistent(is_kernel<true, 8, false>, sh, s, g, dp, ia, sh.lay, sh.G)
+                   : launch_persistent(is_kernel<false, 8, false>, sh, s, g, dp, ia, sh.lay, sh.G);
+        else
+            e = qc ? launch_persistent(is_kernel<true, 32, false>, sh, s, g, dp, ia, sh.lay, sh.G)
+                   : launch_persistent(is_kernel<false, 32, false>, sh, s, g, dp, ia, sh.lay, sh.G);
+        if (e != cudaSuccess) st = TSX_ECUDA;
+    }
+    if (st == TSX_OK) {
+        reduce_kernel<<<nb, kRedBlock, 0, s>>>(ia.wfail, N, (double *)(B + off_p));
+        finish_kernel<<<1, 32, 0, s>>>((const double *)(B + off_p), nb, (double *)(B + off_o));
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess) st = TSX_ECUDA;
+    }
+    if (st == TSX_OK &&
+        (cudaMemcpyAsync(sums, B + off_o, sizeof(sums), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(&c, ia.ctr, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         (fail_out && cudaMemcpyAsync(fail_out, ia.fail_out, N, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+         (logw_out && cudaMemcpyAsync(logw_out, ia.logw_out, N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
+         cudaStreamSynchronize(s) != cudaSuccess))
+        st = TSX_ECUDA;
+    if (st == TSX_OK) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        out->sum_w = sums[0];
+        out->sum_w2 = sums[1];
+        out->fer = sums[0] / (double)N;
+        out->var = (sums[1] / (double)N - out->fer * out->fer) / (double)N;
+        out->n_fail = (int64_t)c.n_fail;
+        out->decodes = (int64_t)c.decodes;
+        out->iterations = (int64_t)c.iterations;
+        out->edge_updates = (int64_t)c.edge_updates;
+        out->ms = ms;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFreeAsync(blk, s);
+    cudaStreamSynchronize(s);
+    return st;
+}

@@ -65,6 +65,10 @@ cudaError_t launch_decode(const DevCode &g, const DecodeParams &dp, const EnumBu
 // failing candidate (reads the records and x* written by the decoder).
 cudaError_t launch_sieve(const DevCode &g, const EnumBuffers &b, int decoder, int num_sms, cudaStream_t st);
 
+// Shape of the importance-sampling kernel (two samples per lane); false if
+// the 16-bit bias bounds or the shared memory do not allow it.
+bool plan_is_shape(const DevCode &g, const DecodeParams &dp, LaunchShape *sh, int num_sms);
+
 // Whether one codeword of g fits the shared memory of a CTA.
 bool decode_fits(const DevCode &g, int decoder);
 

@@ -61,6 +61,7 @@ struct Counters {
     unsigned long long n_cand_total;  // canonical candidates written
     unsigned long long acyclic;
     unsigned long long next_sieve;  // work queue of the sieve kernel
+    unsigned long long n_fail;      // importance sampling: failing samples
     unsigned int n_ts;
     unsigned int err;               // bit flags, see kErr*
 };
