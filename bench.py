@@ -9,6 +9,14 @@ device tables) are resident when the timed region starts; L2 is flushed
 (a 256 MB write) before every timed step, outside its CUDA-event bracket.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --workload batch32 [--tune]   # 32 codes, one graph-replayed batch
+  python bench.py --workload serve [--jobs N --load F]   # Poisson job stream, p50/p99
+
+The batch32 workload enumerates the 32 QC codes of uneven sizes (4 x 16 to
+4 x 32 bases, Z 64 to 384) together: per-code candidate kernels and sieves,
+one multi-code persistent decode launch, the whole step captured once in a
+CUDA graph and replayed; the same codes run one enumerate_ts() at a time are
+timed beside it ("serial").
 
 Multi-GPU (torchrun): every rank enumerates its own code of the same shape
 (rank r uses seed offset r: independent problems, weak scaling); no
@@ -52,7 +60,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="peg1008", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="peg1008", choices=sorted(synth.WORKLOADS) + ["batch32", "serve"])
+    ap.add_argument("--jobs", type=int, default=120, help="serve: jobs in the Poisson stream")
+    ap.add_argument("--load", type=float, default=0.8, help="serve: offered load (fraction of the plain method's "
+                                                             "throughput)")
+    ap.add_argument("--tune", action="store_true", help="batch32: pick each code's tile with tune_tile()")
     ap.add_argument("--decoder", default="nms16", choices=["nms16", "nms8", "spa"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -67,6 +79,10 @@ def rank_world():
 
 
 def workload_for(name, rank):
+    if name == "batch32":  # the reference arm samples the first code of the batch
+        return dict(code=synth.batch_codes([100 + 32 * rank])[0], **BATCH)
+    if name == "serve":  # the reference arm samples the largest code of the stream
+        return dict(code=synth.serving_codes(2026, 8)[4], **SERVE_ENUM)
     w = dict(synth.workload(name))
     if rank:
         if name == "peg1008":
@@ -332,9 +348,284 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+BATCH = dict(K=20, base_llr=16, amp_steps=10, max_size=2, cycle_len=0)
+
+
+def run_batch(args):
+    import torch
+    import paper_2208_05795_gb300 as tsx
+    from paper_2208_05795_gb300 import build as tsx_build
+
+    rank, world, local = rank_world()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    tsx_build.build()
+    # rank r takes seeds 100 + 32 r .. 131 + 32 r: independent batches of the same shape
+    codes = synth.batch_codes(range(100 + 32 * rank, 132 + 32 * rank))
+    stream = torch.cuda.Stream()
+    handles = [tsx.load_code(c, stream=stream) for c in codes]
+    params = dict(BATCH, decoder=args.decoder)
+    if args.decoder == "nms8":
+        params["sat"] = 127
+    base = tsx.make_params(**params)
+    plist = [tsx.tune_tile(h, base, stream=stream)[0] if args.tune else base for h in handles]
+    if args.tune and len({p.decoder for p in plist}) > 1:
+        plist = [p if p.decoder == base.decoder else tsx.make_params(**dict(params, warps_per_cta=p.warps_per_cta))
+                 for p in plist]
+    batch = tsx.batch_create(handles, plist, stream=stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        tsx.batch_run(batch, stream=stream)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        tsx.batch_run(batch, stream=stream)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    times = []
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                graph.replay()
+                e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    s = tsx.batch_stats(batch)
+    total_ms = sum(times)
+    eu, dec, nts = float(s["edge_updates"]) * args.steps, float(s["decodes"]) * args.steps, s["n_ts"]
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        e = torch.tensor([eu, dec], dtype=torch.float64, device="cuda")
+        dist.all_reduce(e)
+        eu, dec = float(e[0].item()), float(e[1].item())
+    value = eu / (total_ms / 1e3)
+
+    # the same codes one enumerate_ts() at a time (eager, per-code launches)
+    serial_ms = []
+    for _ in range(max(1, min(2, args.steps))):
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lists = [tsx.enumerate_ts(h, p, stream=stream) for h, p in zip(handles, plist)]
+            e1.record(stream)
+        e1.synchronize()
+        serial_ms.append(e0.elapsed_time(e1))
+        del lists
+
+    # end to end: load the 32 codes from host arrays, create, run, read back every result
+    e2e = None
+    if args.e2e_steps > 0:
+        wall, eu2, h2d, d2h = 0.0, 0, 0, 0
+        for _ in range(args.e2e_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hs = [tsx.load_code(c, stream=stream) for c in codes]
+            b2 = tsx.batch_create(hs, plist, stream=stream)
+            tsx.batch_run(b2, stream=stream)
+            views = [tsx.batch_view(b2, i) for i in range(len(hs))]
+            wall += time.perf_counter() - t0
+            eu2 += sum(v["stats"]["edge_updates"] for v in views)
+            h2d = sum(c.shifts.nbytes for c in codes)
+            d2h = sum(sum(v[k].nbytes for k in ("cand_vars", "cand_thr", "cand_thr_f", "cand_ts", "cand_flags",
+                                                "cand_decodes", "cand_iters", "a", "b", "orbit", "count", "thr",
+                                                "flags", "thr_f")) + 4 * sum(len(k) + 4 for k in v["keys"])
+                      for v in views)
+            del b2, hs
+        e2e = {"value": eu2 / wall, "unit": "edge-updates/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peak = INT_LANES_PER_SM * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
+    ms_step = total_ms / args.steps
+    achieved = ALG_OPS_PER_EDGE * float(s["edge_updates"]) / (ms_step / 1e3) / 1e12
+    line = {
+        "metric": "impulse-decode edge-updates/s",
+        "value": value,
+        "unit": "edge-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int8" if args.decoder == "nms8" else "int16",
+        "data": "synthetic",
+        "config": {"workload": "batch32", "codes": len(codes), "n_cand": int(s["n_cand"]),
+                   "n_range": [min(c.n for c in codes), max(c.n for c in codes)], "decoder": args.decoder,
+                   **BATCH, "tuned": bool(args.tune), "tiles": sorted({p.warps_per_cta for p in plist}),
+                   "multi_code_launch": batch.multi_launch, "cuda_graph": True,
+                   "parallelism": f"replicas{world}", "l2": "flushed before each step (256 MB write)"},
+        "decodes_per_s": dec / (total_ms / 1e3),
+        "n_ts": int(nts),
+        "serial_ms_per_step": statistics.median(serial_ms),
+        "batch_speedup_vs_serial": statistics.median(serial_ms) / ms_step,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "note": "whole step (candidates, decode, sieve) against the decode's ALU bound"},
+        "cpu_baseline": None,
+        "e2e": e2e,
+        "gpu_launches": (len(codes) * 6 + 1) * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+SERVE_ENUM = dict(K=20, base_llr=16, amp_steps=10, max_size=2, cycle_len=0)
+
+
+def serve_jobs(n_jobs, seed=2026):
+    """The serving stream's jobs (arrival times are drawn later from the
+    offered load): 8 resident QC codes (bases 3x6 .. 4x24, Z 16 .. 512,
+    n <= 10,000); 3 in 4 jobs enumerate 1K .. 100K candidates (log-uniform)
+    of a code, the others run 10^6 importance samples toward a trapping set
+    of a code found beforehand, at Eb/N0 uniform in [3, 5] dB."""
+    rng = np.random.default_rng(seed)
+    codes = synth.serving_codes(seed, 8)
+    jobs = []
+    for j in range(n_jobs):
+        c = int(rng.integers(0, len(codes)))
+        if rng.random() < 0.75:
+            ncand = int(np.exp(rng.uniform(np.log(1e3), np.log(1e5))))
+            jobs.append(("enum", c, dict(SERVE_ENUM, cand_end=ncand)))
+        else:
+            jobs.append(("is", c, dict(ebn0_db=float(rng.uniform(3.0, 5.0)), mu=1.0, n_samples=1_000_000,
+                                        job_key=1000 + j)))
+    return codes, jobs
+
+
+def run_serve(args):
+    import torch
+    import paper_2208_05795_gb300 as tsx
+    from paper_2208_05795_gb300 import build as tsx_build
+
+    rank, world, local = rank_world()
+    torch.cuda.set_device(local)
+    if world > 1 and rank != 0:
+        return  # the serving stream runs on one GPU: replicas only
+    tsx_build.build()
+    codes, jobs = serve_jobs(args.jobs)
+    handles = [tsx.load_code(c) for c in codes]
+    # a trapping set per code for the importance-sampling jobs: the lowest
+    # threshold among the first 2000 candidates' sets
+    ts_of = []
+    for h in handles:
+        v = tsx.ts_list_view(tsx.enumerate_ts(h, **dict(SERVE_ENUM, cand_end=2000)))
+        thr = np.where(v["thr"] >= 0, v["thr"], 1 << 30)
+        ts_of.append(v["keys"][int(np.argmin(thr))] if len(thr) else (0,))
+
+    def submit(srv, job):
+        kind, c, p = job
+        if kind == "enum":
+            return srv.submit_enumerate(handles[c], **p)
+        return srv.submit_is_fer(handles[c], ts_of[c], **p)
+
+    def stream(srv, arrivals):
+        ids = []
+        t0 = time.perf_counter()
+        for job, t in zip(jobs, arrivals):
+            d = t - (time.perf_counter() - t0)
+            if d > 0:
+                time.sleep(d)
+            ids.append(submit(srv, job))
+        srv.drain()
+        res = [srv.wait(i) for i in ids]
+        st = srv.stats()
+        for i in ids:
+            srv.release(i)
+        return res, st
+
+    # warm-up, then the plain method's throughput with every job queued at once
+    with tsx.Server(serial=1) as srv:
+        for job in jobs[:3]:
+            srv.wait(submit(srv, job))
+        srv.reset_stats()
+        _, cal = stream(srv, [0.0] * len(jobs))
+    mean_service_s = cal["makespan_ms"] / 1e3 / len(jobs)
+    rate = args.load / mean_service_s
+    arrivals = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, len(jobs)))
+    arrivals -= arrivals[0]
+    out = {}
+    for mode, kw in (("plain", dict(serial=1)), ("served", dict(max_jobs=8))):
+        with Clocks(local) as clk:
+            with tsx.Server(**kw) as srv:
+                res, st = stream(srv, list(arrivals))
+        out[mode] = (res, st, clk.summary())
+    rp, sp, _ = out["plain"]
+    rs, ss, clocks = out["served"]
+    same = all(a["status"] == b["status"] == 0 and
+               (a["enum_stats"]["n_ts"], a["enum_stats"]["decodes"], a["is_result"]["sum_w"],
+                a["is_result"]["n_fail"]) ==
+               (b["enum_stats"]["n_ts"], b["enum_stats"]["decodes"], b["is_result"]["sum_w"],
+                b["is_result"]["n_fail"]) for a, b in zip(rp, rs))
+    n_enum = sum(1 for j in jobs if j[0] == "enum")
+    line = {
+        "metric": "serving job latency p99",
+        "value": ss["p99_ms"],
+        "unit": "ms",
+        "n_gpus": 1,
+        "steps": len(jobs),
+        "warmup": 3,
+        "ms_per_step": ss["mean_ms"],
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int16",
+        "data": "synthetic",
+        "config": {"workload": "serve", "jobs": len(jobs), "enumeration_jobs": n_enum,
+                   "is_jobs": len(jobs) - n_enum, "codes": len(codes),
+                   "n_range": [min(c.n for c in codes), max(c.n for c in codes)],
+                   "offered_load": args.load, "arrival_rate_per_s": rate,
+                   "mean_service_ms_plain": mean_service_s * 1e3, "max_jobs": 8,
+                   "l2": "inputs resident; not flushed (a stream of jobs)"},
+        "p50_ms": ss["p50_ms"], "p90_ms": ss["p90_ms"], "p99_ms": ss["p99_ms"], "mean_ms": ss["mean_ms"],
+        "plain": {"p50_ms": sp["p50_ms"], "p90_ms": sp["p90_ms"], "p99_ms": sp["p99_ms"], "mean_ms": sp["mean_ms"],
+                  "edge_updates_per_s": sp["edge_updates_per_s"], "makespan_ms": sp["makespan_ms"]},
+        "edge_updates_per_s": ss["edge_updates_per_s"],
+        "makespan_ms": ss["makespan_ms"],
+        "max_concurrent_jobs": ss["max_concurrent"],
+        "hbm_peak_bytes": ss["hbm_peak_bytes"],
+        "results_identical_to_plain": bool(same),
+        "roofline": None,
+        "cpu_baseline": None,
+        "e2e": {"value": ss["p99_ms"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "latency is measured from submit (host) to results copied to host memory"},
+        "gpu_launches": None,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.workload == "serve" and args.impl != "reference":
+        run_serve(args)
+        return
+    if args.workload == "batch32" and args.impl != "reference":
+        run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

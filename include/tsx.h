@@ -166,8 +166,8 @@ typedef struct {
  * (1 for CSR codes); count[i] = candidates that produced it; thr[i] /
  * thr_f[i] = smallest threshold amplitude among them (min-sum integer A /
  * sum-product eps; the other is -1); flags[i] bit 0 = elementary (every
- * check touches it at most twice), bits 1-2 = sieve (1: Tree(X), 2:
- * Tree(TS(X))); key: vars[var_off[i] .. var_off[i] + a[i]) ascending
+ * check touches it at most twice), bit 1 = some candidate reached it as
+ * Tree(X), bit 2 = some candidate reached it as Tree(TS(X)); key: vars[var_off[i] .. var_off[i] + a[i]) ascending
  * (the lexicographically smallest circulant shift).
  * Per candidate c (if records were kept): cand_vars[4c..4c+3] canonical
  * impulse set (-1 padded); cand_thr[c] / cand_thr_f[c] threshold or -1;
@@ -197,6 +197,47 @@ TSX_API int ts_list_view(tsx_ts_list *list, tsx_ts_view *view);
 TSX_API int ts_list_stats(tsx_ts_list *list, tsx_enum_stats *stats);
 
 TSX_API void free_ts_list(tsx_ts_list *list);
+
+/* ---- tile autotuner (no counterpart in the paper) ---------------------
+ * Picks the decode tile for `code` under `params`: the number of warps that
+ * share one pair of codewords (1, 2, 4 or 8, at most one warp per 32 rows of
+ * the smallest pass) and, for the int16 min-sum decoder with sat <= 169, int8
+ * message storage (which gives the same results).  Each choice decodes the
+ * first num_sms * 256 canonical candidates once after one warm-up run, timed
+ * with CUDA events on `stream` (synchronizes); the fastest is written to
+ * `tuned` (a copy of params with decoder and warps_per_cta set) and its decode
+ * time to *ms_best (may be NULL).  Float decoder and kernel = 1: tuned =
+ * params.  Errors as for enumerate_ts(). */
+TSX_API int tune_tile(tsx_code *code, const tsx_enum_params *params, void *stream, tsx_enum_params *tuned,
+                      float *ms_best);
+
+/* ---- batches of codes (no counterpart in the paper) -------------------
+ * Enumerates several codes together: the candidate generation and the
+ * sieve run per code, the impulse decodes of all codes run in ONE
+ * persistent launch whose CTAs take the codes in turn and drain each
+ * code's candidate queue (codes of uneven sizes share the SMs).  A batch is
+ * created once (all device memory is allocated and sized there) and run any
+ * number of times; batch_run() enqueues only kernels and memsets, so it can
+ * be captured in a CUDA graph and replayed.
+ *   codes, params: host arrays of n; every code must be on the current
+ *     device; params[i].kernel = 1 (one codeword per group) and codes whose
+ *     min-sum parameters leave the two-codeword kernel's 16-bit bounds, the
+ *     float decoder, or a mix of QC and CSR codes or of decoders, fall back to
+ *     one decode launch per code (batch_multi_launch() returns 0).
+ * Results of run k are read with batch_view(batch, i, ...) after the stream
+ * has reached the end of that run; batch_view synchronizes `stream` of the
+ * last batch_run.  Errors as for enumerate_ts(). */
+typedef struct tsx_batch tsx_batch;
+TSX_API int batch_create(tsx_code *const *codes, const tsx_enum_params *params, int32_t n, void *stream,
+                         tsx_batch **out);
+TSX_API int batch_run(tsx_batch *batch, void *stream);
+TSX_API int batch_size(const tsx_batch *batch);
+TSX_API int batch_multi_launch(const tsx_batch *batch);
+/* Results of code i of the last run (same contents as ts_list_view()). */
+TSX_API int batch_view(tsx_batch *batch, int32_t i, tsx_ts_view *view);
+/* Sums of the device counters of all codes of the last run. */
+TSX_API int batch_stats(tsx_batch *batch, tsx_enum_stats *total);
+TSX_API void batch_free(tsx_batch *batch);
 
 /* ---- importance-sampling FER toward a trapping set ------------------ */
 /* The weighting step the paper takes from Cole (Sec. II-III: trapping sets
@@ -243,6 +284,98 @@ TSX_API void is_params_default(tsx_is_params *p);
  * bounds), TSX_ENOMEM, TSX_ECUDA. */
 TSX_API int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *params,
                             void *stream, tsx_is_result *out, uint8_t *fail_out, double *logw_out);
+
+/* ---- serving runtime (no counterpart in the paper) --------------------
+ * A request loop over resident codes: enumeration and importance-sampling
+ * jobs are submitted as they arrive, admitted in arrival order while their
+ * device-memory footprint fits the server's budget and a job slot is free
+ * (a job that does not fit may be overtaken by later ones that do, for at
+ * most backfill_ms), and run concurrently on a pool of streams: each job's
+ * persistent launches are sized to its work and split into chunks, so that
+ * jobs arriving while others are on the GPU get SMs at the next chunk
+ * boundary; small jobs run on high-priority streams, large ones on
+ * low-priority streams, at most max_large of them at once.  A job's results
+ * are the same as those of the stand-alone entry point with the same
+ * parameters (chunking and grid size do not change them).  One host thread
+ * of the server drives the GPU; the calls below may come from any thread. */
+typedef struct tsx_server tsx_server;
+
+enum { TSX_JOB_ENUMERATE = 0, TSX_JOB_IS_FER = 1 };
+
+typedef struct {
+    int32_t max_jobs;          /* jobs on the device at once (default 8) */
+    int32_t serial;            /* 1: the plain method -- one job at a time in arrival order,
+                                  each as one full-GPU launch per step (for comparison) */
+    int32_t device;            /* CUDA device; -1 = the current one */
+    int64_t hbm_bytes;         /* device memory the admitted jobs may hold together;
+                                  0 = half of the free memory at creation */
+    int64_t chunk_candidates;  /* decode launch granularity of enumeration jobs (default 16384) */
+    int64_t chunk_samples;     /* launch granularity of IS jobs (default 32768) */
+    double small_work;         /* jobs whose estimated edge updates -- candidates x (s+1)/2 x E x K/2,
+                                  or samples x E x K/2 -- are at most this run on high-priority
+                                  streams (default 2e10) */
+    double backfill_ms;        /* how long a job that does not fit may be overtaken (default 100) */
+    int32_t max_large;         /* large (low-priority) jobs on the device at once, in arrival
+                                  order among themselves (default 1) */
+} tsx_server_params;
+
+typedef struct {
+    int32_t kind;                  /* TSX_JOB_* */
+    tsx_code *code;                /* a loaded code; keep it loaded until the job is done */
+    tsx_enum_params enum_params;   /* TSX_JOB_ENUMERATE (the results are kept as by enumerate_ts) */
+    tsx_is_params is_params;       /* TSX_JOB_IS_FER */
+    const int32_t *ts_vars;        /* TSX_JOB_IS_FER: host, a variable nodes (copied at submit) */
+    int32_t a;
+} tsx_job;
+
+typedef struct {
+    int32_t status;        /* TSX_OK, TSX_EAGAIN (queued or running) or the job's error */
+    int32_t kind;
+    int32_t high_priority; /* ran on a high-priority stream */
+    int32_t grid_sms;      /* SMs its persistent launches were sized to */
+    int64_t device_bytes;  /* admitted footprint */
+    double queue_ms;       /* submit -> admission */
+    double run_ms;         /* admission -> results on the host */
+    double latency_ms;     /* submit -> results on the host */
+    tsx_enum_stats enum_stats;
+    tsx_is_result is_result;
+} tsx_job_result;
+
+typedef struct {
+    int64_t submitted, done, failed, running, queued;
+    double p50_ms, p90_ms, p99_ms, max_ms, mean_ms;  /* latency of the completed jobs */
+    double mean_queue_ms;
+    double makespan_ms;        /* first submit -> last completion */
+    int64_t edge_updates, decodes;
+    double edge_updates_per_s; /* edge_updates / makespan */
+    int64_t hbm_peak_bytes;    /* largest admitted footprint held at once */
+    int32_t max_concurrent;    /* most jobs on the device at once */
+} tsx_server_stats;
+
+/* Defaults as stated above (max_jobs 8, serial 0, device -1, ...). */
+TSX_API void server_params_default(tsx_server_params *p);
+/* Creates the server and its worker thread.  Errors: TSX_EINVAL, TSX_ECUDA. */
+TSX_API int server_create(const tsx_server_params *params, tsx_server **out);
+/* Queues a job and returns its id.  The parameters are validated and the
+ * footprint computed here: TSX_EINVAL / TSX_EUNSUPPORTED as for the
+ * stand-alone call, TSX_ENOMEM if the job alone exceeds the budget. */
+TSX_API int server_submit(tsx_server *server, const tsx_job *job, uint64_t *id);
+/* TSX_EAGAIN while the job is queued or running; TSX_ENOTFOUND for an
+ * unknown or released id; otherwise fills `result` and returns its status. */
+TSX_API int server_poll(tsx_server *server, uint64_t id, tsx_job_result *result);
+/* As server_poll, but waits up to timeout_ms (< 0: without limit). */
+TSX_API int server_wait(tsx_server *server, uint64_t id, double timeout_ms, tsx_job_result *result);
+/* Results of a completed enumeration job (valid until server_release). */
+TSX_API int server_job_view(tsx_server *server, uint64_t id, tsx_ts_view *view);
+/* Forgets a completed job and its results (TSX_EAGAIN if not completed). */
+TSX_API int server_release(tsx_server *server, uint64_t id);
+/* Waits until every submitted job has completed. */
+TSX_API int server_drain(tsx_server *server);
+TSX_API int server_stats(tsx_server *server, tsx_server_stats *stats);
+/* Clears the latency record and counters (jobs in flight are kept). */
+TSX_API void server_reset_stats(tsx_server *server);
+/* Waits for the jobs on the device, drops the queued ones, frees everything. */
+TSX_API void server_destroy(tsx_server *server);
 
 /* ---- decoding without allocation (no counterpart in the paper) --------
  * For callers that cannot allocate device memory -- a latency-critical host

@@ -6,9 +6,16 @@ The hot path of the modified Cole importance-sampling method (arXiv
 """
 from ._tsx import (  # noqa: F401
     DECODERS,
+    Batch,
     Code,
+    Server,
     TsList,
     TsxError,
+    batch_create,
+    batch_free,
+    batch_run,
+    batch_stats,
+    batch_view,
     code_info,
     decode_thresholds_noalloc,
     enum_params_default,
@@ -20,7 +27,9 @@ from ._tsx import (  # noqa: F401
     lib,
     load_code,
     make_params,
+    server_params_default,
     strerror,
     ts_list_stats,
     ts_list_view,
+    tune_tile,
 )

@@ -73,6 +73,35 @@ class IsResult(C.Structure):
                 ("iterations", C.c_int64), ("edge_updates", C.c_int64), ("ms", C.c_double)]
 
 
+class ServerParams(C.Structure):
+    _fields_ = [("max_jobs", C.c_int32), ("serial", C.c_int32), ("device", C.c_int32), ("hbm_bytes", C.c_int64),
+                ("chunk_candidates", C.c_int64), ("chunk_samples", C.c_int64), ("small_work", C.c_double),
+                ("backfill_ms", C.c_double), ("max_large", C.c_int32)]
+
+
+class Job(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("code", C.c_void_p), ("enum_params", EnumParams), ("is_params", IsParams),
+                ("ts_vars", C.c_void_p), ("a", C.c_int32)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("kind", C.c_int32), ("high_priority", C.c_int32), ("grid_sms", C.c_int32),
+                ("device_bytes", C.c_int64), ("queue_ms", C.c_double), ("run_ms", C.c_double),
+                ("latency_ms", C.c_double), ("enum_stats", EnumStats), ("is_result", IsResult)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("done", C.c_int64), ("failed", C.c_int64), ("running", C.c_int64),
+                ("queued", C.c_int64), ("p50_ms", C.c_double), ("p90_ms", C.c_double), ("p99_ms", C.c_double),
+                ("max_ms", C.c_double), ("mean_ms", C.c_double), ("mean_queue_ms", C.c_double),
+                ("makespan_ms", C.c_double), ("edge_updates", C.c_int64), ("decodes", C.c_int64),
+                ("edge_updates_per_s", C.c_double), ("hbm_peak_bytes", C.c_int64), ("max_concurrent", C.c_int32)]
+
+
+TSX_JOB_ENUMERATE, TSX_JOB_IS_FER = 0, 1
+TSX_ENOTFOUND, TSX_EAGAIN = -7, -8
+
+
 class TsView(C.Structure):
     _fields_ = [("stats", EnumStats), ("n_ts", C.c_int64), ("a", I32), ("b", I32), ("orbit", I32),
                 ("count", I32), ("thr", I32), ("flags", I32), ("thr_f", F32), ("var_off", I64),
@@ -118,6 +147,44 @@ def lib():
             L.is_fer_estimate.restype = C.c_int
             L.decode_thresholds_noalloc.argtypes = [vp, C.POINTER(EnumParams), vp, C.c_int64, vp, vp, vp, vp, vp]
             L.decode_thresholds_noalloc.restype = C.c_int
+            L.tune_tile.argtypes = [vp, C.POINTER(EnumParams), vp, C.POINTER(EnumParams), C.POINTER(C.c_float)]
+            L.tune_tile.restype = C.c_int
+            L.batch_create.argtypes = [C.POINTER(vp), C.POINTER(EnumParams), C.c_int32, vp, C.POINTER(vp)]
+            L.batch_create.restype = C.c_int
+            L.batch_run.argtypes = [vp, vp]
+            L.batch_run.restype = C.c_int
+            L.batch_size.argtypes = [vp]
+            L.batch_size.restype = C.c_int
+            L.batch_multi_launch.argtypes = [vp]
+            L.batch_multi_launch.restype = C.c_int
+            L.batch_view.argtypes = [vp, C.c_int32, C.POINTER(TsView)]
+            L.batch_view.restype = C.c_int
+            L.batch_stats.argtypes = [vp, C.POINTER(EnumStats)]
+            L.batch_stats.restype = C.c_int
+            L.batch_free.argtypes = [vp]
+            L.batch_free.restype = None
+            L.server_params_default.argtypes = [C.POINTER(ServerParams)]
+            L.server_params_default.restype = None
+            L.server_create.argtypes = [C.POINTER(ServerParams), C.POINTER(vp)]
+            L.server_create.restype = C.c_int
+            L.server_submit.argtypes = [vp, C.POINTER(Job), C.POINTER(C.c_uint64)]
+            L.server_submit.restype = C.c_int
+            L.server_poll.argtypes = [vp, C.c_uint64, C.POINTER(JobResult)]
+            L.server_poll.restype = C.c_int
+            L.server_wait.argtypes = [vp, C.c_uint64, C.c_double, C.POINTER(JobResult)]
+            L.server_wait.restype = C.c_int
+            L.server_job_view.argtypes = [vp, C.c_uint64, C.POINTER(TsView)]
+            L.server_job_view.restype = C.c_int
+            L.server_release.argtypes = [vp, C.c_uint64]
+            L.server_release.restype = C.c_int
+            L.server_drain.argtypes = [vp]
+            L.server_drain.restype = C.c_int
+            L.server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+            L.server_stats.restype = C.c_int
+            L.server_reset_stats.argtypes = [vp]
+            L.server_reset_stats.restype = None
+            L.server_destroy.argtypes = [vp]
+            L.server_destroy.restype = None
             _lib = L
     return _lib
 
@@ -251,6 +318,10 @@ def ts_list_view(lst: TsList, check: bool = True) -> dict:
     st = lib().ts_list_view(lst.h, C.byref(v))
     if check:
         _check(st, "ts_list_view")
+    return _view_dict(v, st)
+
+
+def _view_dict(v, st) -> dict:
     nts, nc = int(v.n_ts), int(v.n_cand)
     out = {"status": st, "stats": {k: getattr(v.stats, k) for k, _ in EnumStats._fields_}}
     for k in ("a", "b", "orbit", "count", "thr", "flags"):
@@ -278,6 +349,79 @@ def free_ts_list(lst: TsList):
     if lst.h:
         lib().free_ts_list(lst.h)
         lst.h = None
+
+
+def tune_tile(code: Code, params=None, stream=None, **kw):
+    """tune_tile(): returns (tuned EnumParams, decode ms of the best tile)."""
+    p = params if isinstance(params, EnumParams) else make_params(**(params or {}), **kw)
+    t = EnumParams()
+    ms = C.c_float()
+    _check(lib().tune_tile(code.h, C.byref(p), _stream_handle(stream), C.byref(t), C.byref(ms)), "tune_tile")
+    return t, float(ms.value)
+
+
+class Batch:
+    """A batch of codes enumerated together (batch_create)."""
+
+    def __init__(self, handle, codes):
+        self.h = handle
+        self.codes = list(codes)  # keeps the codes alive
+
+    def __len__(self):
+        return int(lib().batch_size(self.h))
+
+    @property
+    def multi_launch(self) -> bool:
+        return bool(lib().batch_multi_launch(self.h))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().batch_free(self.h)
+            self.h = None
+
+
+def batch_create(codes, params, stream=None) -> Batch:
+    """batch_create(): codes is a list of Code, params one EnumParams (or
+    dict) for all of them or a list with one per code."""
+    n = len(codes)
+    if isinstance(params, (list, tuple)):
+        ps = [p if isinstance(p, EnumParams) else make_params(**p) for p in params]
+    else:
+        p0 = params if isinstance(params, EnumParams) else make_params(**(params or {}))
+        ps = [p0] * n
+    if len(ps) != n:
+        raise ValueError("one parameter set per code")
+    harr = (C.c_void_p * n)(*[c.h for c in codes])
+    parr = (EnumParams * n)(*ps)
+    h = C.c_void_p()
+    _check(lib().batch_create(harr, parr, n, _stream_handle(stream), C.byref(h)), "batch_create")
+    return Batch(h, codes)
+
+
+def batch_run(batch: Batch, stream=None):
+    _check(lib().batch_run(batch.h, _stream_handle(stream)), "batch_run")
+
+
+def batch_view(batch: Batch, i: int, check: bool = True) -> dict:
+    v = TsView()
+    st = lib().batch_view(batch.h, int(i), C.byref(v))
+    if check:
+        _check(st, "batch_view")
+    return _view_dict(v, st)
+
+
+def batch_stats(batch: Batch, check: bool = True) -> dict:
+    s = EnumStats()
+    st = lib().batch_stats(batch.h, C.byref(s))
+    if check:
+        _check(st, "batch_stats")
+    return {k: getattr(s, k) for k, _ in EnumStats._fields_}
+
+
+def batch_free(batch: Batch):
+    if batch.h:
+        lib().batch_free(batch.h)
+        batch.h = None
 
 
 def is_params_default() -> IsParams:
@@ -320,3 +464,112 @@ def decode_thresholds_noalloc(code: Code, cand_vars_ptr: int, n_cand: int, thr_p
     if check:
         _check(st, "decode_thresholds_noalloc")
     return st
+
+
+def _struct_dict(x) -> dict:
+    out = {}
+    for k, _ in x._fields_:
+        v = getattr(x, k)
+        out[k] = _struct_dict(v) if isinstance(v, C.Structure) else v
+    return out
+
+
+def server_params_default() -> ServerParams:
+    p = ServerParams()
+    lib().server_params_default(C.byref(p))
+    return p
+
+
+class Server:
+    """The serving runtime (server_create ... server_destroy).  Codes given to
+    submit_* must stay alive until their jobs complete (the server keeps a
+    reference until the job is released)."""
+
+    def __init__(self, **kw):
+        p = server_params_default()
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown server parameter {k}")
+            setattr(p, k, v)
+        h = C.c_void_p()
+        _check(lib().server_create(C.byref(p), C.byref(h)), "server_create")
+        self.h = h
+        self.params = p
+        self._keep = {}
+
+    def _submit(self, job, keep) -> int:
+        jid = C.c_uint64()
+        _check(lib().server_submit(self.h, C.byref(job), C.byref(jid)), "server_submit")
+        self._keep[jid.value] = keep
+        return int(jid.value)
+
+    def submit_enumerate(self, code: Code, params=None, **kw) -> int:
+        p = params if isinstance(params, EnumParams) else make_params(**(params or {}), **kw)
+        job = Job(kind=TSX_JOB_ENUMERATE, code=code.h, enum_params=p)
+        return self._submit(job, code)
+
+    def submit_is_fer(self, code: Code, ts_vars, **kw) -> int:
+        p = is_params_default()
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k}")
+            setattr(p, k, v)
+        T = _i32(ts_vars)
+        job = Job(kind=TSX_JOB_IS_FER, code=code.h, is_params=p, ts_vars=T.ctypes.data_as(C.c_void_p), a=T.size)
+        return self._submit(job, code)
+
+    def poll(self, jid: int):
+        """None while queued or running, else the result dict."""
+        r = JobResult()
+        st = lib().server_poll(self.h, jid, C.byref(r))
+        if st == TSX_EAGAIN:
+            return None
+        if st == TSX_ENOTFOUND:
+            _check(st, "server_poll")
+        return _struct_dict(r)
+
+    def wait(self, jid: int, timeout_ms: float = -1.0):
+        r = JobResult()
+        st = lib().server_wait(self.h, jid, float(timeout_ms), C.byref(r))
+        if st == TSX_EAGAIN:
+            return None
+        if st == TSX_ENOTFOUND:
+            _check(st, "server_wait")
+        return _struct_dict(r)
+
+    def view(self, jid: int, check: bool = True) -> dict:
+        v = TsView()
+        st = lib().server_job_view(self.h, jid, C.byref(v))
+        if check:
+            _check(st, "server_job_view")
+        return _view_dict(v, st)
+
+    def release(self, jid: int):
+        _check(lib().server_release(self.h, jid), "server_release")
+        self._keep.pop(jid, None)
+
+    def drain(self):
+        _check(lib().server_drain(self.h), "server_drain")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(lib().server_stats(self.h, C.byref(s)), "server_stats")
+        return _struct_dict(s)
+
+    def reset_stats(self):
+        lib().server_reset_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

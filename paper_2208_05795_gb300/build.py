@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtsx.so")
-SOURCES = ["api.cu", "cand.cu", "decode.cu", "decode_i16.cu", "decode_i8.cu", "decode_spa.cu", "sieve.cu", "noalloc.cu", "isfer.cu"]
+SOURCES = ["api.cu", "cand.cu", "decode.cu", "decode_i16.cu", "decode_i8.cu", "decode_spa.cu", "sieve.cu", "noalloc.cu", "isfer.cu",
+           "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -67,7 +68,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcudart"]
+    cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

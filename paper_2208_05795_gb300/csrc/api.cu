@@ -43,6 +43,21 @@ struct tsx_ts_list {
     Counters *ctr = nullptr;
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, decode, sieve, compact, end
     int *ts_off = nullptr, *ts_count = nullptr, *ts_thr = nullptr, *slot_map = nullptr;
+    // candidate generation
+    std::vector<long long> raw_off;
+    long long raw_total = 0, n_chunks = 0, paths = 0;
+    int cyc_l = 0;
+    bool cycles = false, events = true;
+    long long *d_raw_off = nullptr, *d_chunk_off = nullptr, *d_cyc_off = nullptr;
+    int *d_chunk_cnt = nullptr, *d_cyc_cnt = nullptr;
+    // decode launch shape: one launch over the whole range (dchunk = 0) or
+    // one launch per dchunk candidates, each with its own queue word
+    long long dchunk = 0, n_dchunks = 0, range_end = 0;
+    unsigned long long *d_queues = nullptr;
+    int grid_sms = 0;
+    // sizing only: allocations are counted, not made
+    bool dry = false;
+    long long bytes = 0;
     // host results
     bool oom = false;
     bool fetched = false;
@@ -408,8 +423,11 @@ static long long next_pow2(long long x) {
 
 template <class T>
 static T *lalloc(tsx_ts_list *L, size_t count, cudaStream_t s) {
+    const size_t bytes = std::max<size_t>(1, count) * sizeof(T);
+    L->bytes += (long long)((bytes + 255) / 256 * 256);
+    if (L->dry) return nullptr;
     void *p = nullptr;
-    if (cudaMallocAsync(&p, std::max<size_t>(1, count) * sizeof(T), s) != cudaSuccess) {
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
         L->oom = true;
         return nullptr;
     }
@@ -427,14 +445,19 @@ static void release(tsx_ts_list *L) {
         }
 }
 
-extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void *stream, tsx_ts_list **out) {
-    if (!code || !params || !out) return TSX_EINVAL;
+// Validates, sizes and allocates the buffers of one enumeration (no kernel
+// is launched; the raw-set offsets are uploaded).
+// With dry = true nothing is allocated or copied: *out receives a list whose
+// `bytes` is the device memory the real call would take (free it with
+// delete).  dchunk > 0 splits the decode into launches of dchunk candidates;
+// grid_sms > 0 caps the decode and sieve grids at that many SMs.
+static int prepare_list(tsx_code *code, const tsx_enum_params *params, cudaStream_t s, bool events,
+                        tsx_ts_list **out, long long dchunk = 0, int grid_sms = 0, bool dry = false) {
     *out = nullptr;
     int st = check_params(*params);
     if (st != TSX_OK) return st;
     const tsx_enum_params &p = *params;
     const DevCode &g = code->d;
-    cudaStream_t s = (cudaStream_t)stream;
 
     // raw-set offsets per representative (host arithmetic on ball sizes)
     const int n_rep = g.n_rep;
@@ -467,10 +490,23 @@ extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void 
     if (!decode_fits(g, p.decoder)) return TSX_EUNSUPPORTED;
 
     tsx_ts_list *L = new tsx_ts_list();
+    L->dry = dry;
     L->code = code;
     L->st = s;
     L->p = p;
+    L->grid_sms = grid_sms > 0 ? std::min(grid_sms, code->num_sms) : code->num_sms;
+    L->range_end = p.cand_end >= 0 ? std::min<long long>(p.cand_end, cand_bound) : cand_bound;
+    if (dchunk > 0) {
+        L->dchunk = dchunk;
+        L->n_dchunks = std::max<long long>(1, (L->range_end - p.cand_begin + dchunk - 1) / dchunk);
+    }
     L->n_rec = n_rec;
+    L->events = events;
+    L->raw_off = raw_off;
+    L->raw_total = raw_total;
+    L->cycles = cycles;
+    L->cyc_l = l;
+    L->paths = paths;
     L->cap = next_pow2(std::max<long long>(1024, 2 * std::max<long long>(n_rec, 1)));
     L->pool_cap = std::max<long long>(1 << 20, 24 * n_rec);
     if (L->pool_cap > 0xfffffff0LL) L->pool_cap = 0xfffffff0LL;
@@ -479,13 +515,13 @@ extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void 
     dp.alpha_num = p.alpha_num; dp.alpha_shift = p.alpha_shift; dp.amp_steps = p.amp_steps;
     dp.spa_clip = p.spa_clip; dp.spa_amax = p.spa_amax;
 
-    const long long n_chunks = cand_chunks(raw_total);
-    long long *d_raw_off = lalloc<long long>(L, n_rep + 1, s);
-    int *d_chunk_cnt = lalloc<int>(L, n_chunks, s);
-    long long *d_chunk_off = lalloc<long long>(L, n_chunks + 1, s);
+    L->n_chunks = cand_chunks(raw_total);
+    L->d_raw_off = lalloc<long long>(L, n_rep + 1, s);
+    L->d_chunk_cnt = lalloc<int>(L, L->n_chunks, s);
+    L->d_chunk_off = lalloc<long long>(L, L->n_chunks + 1, s);
     int4 *d_cands = lalloc<int4>(L, cand_bound, s);
-    int *d_cyc_cnt = cycles ? lalloc<int>(L, n_rep, s) : nullptr;
-    long long *d_cyc_off = cycles ? lalloc<long long>(L, n_rep + 1, s) : nullptr;
+    L->d_cyc_cnt = cycles ? lalloc<int>(L, n_rep, s) : nullptr;
+    L->d_cyc_off = cycles ? lalloc<long long>(L, n_rep + 1, s) : nullptr;
     EnumBuffers &b = L->b;
     b.cands = d_cands;
     b.cand_begin = p.cand_begin;
@@ -508,69 +544,292 @@ extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void 
     b.pool_cap = (unsigned long long)L->pool_cap;
     L->ctr = lalloc<Counters>(L, 1, s);
     b.ctr = L->ctr;
+    b.queue = L->ctr ? &L->ctr->next_cand : nullptr;
+    b.rec_base = p.cand_begin;
     const long long ts_cap = std::min<long long>(L->cap, std::max<long long>(n_rec, 1));
     L->ts_off = lalloc<int>(L, ts_cap, s);
     L->ts_count = lalloc<int>(L, ts_cap, s);
     L->ts_thr = lalloc<int>(L, ts_cap, s);
     L->slot_map = lalloc<int>(L, L->cap, s);
+    if (L->n_dchunks) L->d_queues = lalloc<unsigned long long>(L, L->n_dchunks, s);
+    if (dry) {
+        *out = L;
+        return TSX_OK;
+    }
     if (L->oom) {
         cudaGetLastError();
         release(L);
         delete L;
         return TSX_ENOMEM;
     }
-
     auto bail = [&](int code_) { release(L); delete L; return code_; };
-    for (cudaEvent_t &e : L->ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return bail(TSX_ECUDA);
-    if (cudaEventRecord(L->ev[0], s) != cudaSuccess) return bail(TSX_ECUDA);
-    if (cudaMemcpyAsync(d_raw_off, raw_off.data(), sizeof(long long) * (n_rep + 1), cudaMemcpyHostToDevice, s) !=
-            cudaSuccess ||
-        cudaMemsetAsync(L->ctr, 0, sizeof(Counters), s) != cudaSuccess ||
-        cudaMemsetAsync(b.tags, 0, sizeof(unsigned long long) * L->cap, s) != cudaSuccess ||
-        cudaMemsetAsync(b.t_count, 0, sizeof(int) * L->cap, s) != cudaSuccess ||
-        cudaMemsetAsync(b.t_thr, 0x7f, sizeof(int) * L->cap, s) != cudaSuccess)
+    if (events)
+        for (cudaEvent_t &e : L->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return bail(TSX_ECUDA);
+    if (cudaMemcpyAsync(L->d_raw_off, L->raw_off.data(), sizeof(long long) * (n_rep + 1), cudaMemcpyHostToDevice,
+                        s) != cudaSuccess)
         return bail(TSX_ECUDA);
-
-    CandArgs ca{};
-    ca.code = g;
-    ca.max_size = p.max_size;
-    ca.raw_off = d_raw_off;
-    ca.raw_total = raw_total;
-    ca.chunk_count = d_chunk_cnt;
-    ca.chunk_off = d_chunk_off;
-    ca.cands = d_cands;
-    ca.ctr = L->ctr;
-    if (launch_cand_ball(ca, n_chunks, false, s) != cudaSuccess ||
-        launch_scan(d_chunk_cnt, n_chunks, d_chunk_off, nullptr, L->ctr, !cycles, s) != cudaSuccess ||
-        launch_cand_ball(ca, n_chunks, true, s) != cudaSuccess)
-        return bail(TSX_ECUDA);
-    if (cycles) {
-        CycleArgs cy{};
-        cy.code = g;
-        cy.l = l;
-        cy.paths = paths;
-        cy.count = d_cyc_cnt;
-        cy.off = d_cyc_off;
-        cy.cands = d_cands;
-        cy.ctr = L->ctr;
-        if (launch_cand_cycle(cy, false, s) != cudaSuccess ||
-            launch_scan(d_cyc_cnt, n_rep, d_cyc_off, d_chunk_off + n_chunks, L->ctr, true, s) != cudaSuccess ||
-            launch_cand_cycle(cy, true, s) != cudaSuccess)
-            return bail(TSX_ECUDA);
-    }
-    if (cudaEventRecord(L->ev[1], s) != cudaSuccess) return bail(TSX_ECUDA);
-    if (launch_decode(g, dp, b, p.warps_per_cta, 0, p.ctas_per_sm, code->num_sms, p.kernel == 1 ? 1 : 0, s) !=
-        cudaSuccess)
-        return bail(TSX_ECUDA);
-    if (cudaEventRecord(L->ev[2], s) != cudaSuccess) return bail(TSX_ECUDA);
-    if (launch_sieve(g, b, p.decoder, code->num_sms, s) != cudaSuccess) return bail(TSX_ECUDA);
-    if (cudaEventRecord(L->ev[3], s) != cudaSuccess) return bail(TSX_ECUDA);
-    if (launch_compact(b, nr, L->ts_off, L->ts_count, L->ts_thr, L->slot_map, s) != cudaSuccess)
-        return bail(TSX_ECUDA);
-    if (cudaEventRecord(L->ev[4], s) != cudaSuccess) return bail(TSX_ECUDA);
     *out = L;
     return TSX_OK;
+}
+
+static int record(tsx_ts_list *L, int i, cudaStream_t s) {
+    if (!L->events) return TSX_OK;
+    return cudaEventRecord(L->ev[i], s) == cudaSuccess ? TSX_OK : TSX_ECUDA;
+}
+
+// counters and table reset, candidate generation
+static int enqueue_front(tsx_ts_list *L, cudaStream_t s) {
+    const DevCode &g = L->code->d;
+    EnumBuffers &b = L->b;
+    L->st = s;
+    L->fetched = false;
+    if (record(L, 0, s) != TSX_OK) return TSX_ECUDA;
+    if (cudaMemsetAsync(L->ctr, 0, sizeof(Counters), s) != cudaSuccess ||
+        cudaMemsetAsync(b.tags, 0, sizeof(unsigned long long) * L->cap, s) != cudaSuccess ||
+        cudaMemsetAsync(b.t_count, 0, sizeof(int) * L->cap, s) != cudaSuccess ||
+        cudaMemsetAsync(b.t_thr, 0x7f, sizeof(int) * L->cap, s) != cudaSuccess ||
+        (L->d_queues &&
+         cudaMemsetAsync(L->d_queues, 0, sizeof(unsigned long long) * L->n_dchunks, s) != cudaSuccess))
+        return TSX_ECUDA;
+    CandArgs ca{};
+    ca.code = g;
+    ca.max_size = L->p.max_size;
+    ca.raw_off = L->d_raw_off;
+    ca.raw_total = L->raw_total;
+    ca.chunk_count = L->d_chunk_cnt;
+    ca.chunk_off = L->d_chunk_off;
+    ca.cands = (int4 *)b.cands;
+    ca.ctr = L->ctr;
+    if (launch_cand_ball(ca, L->n_chunks, false, s) != cudaSuccess ||
+        launch_scan(L->d_chunk_cnt, L->n_chunks, L->d_chunk_off, nullptr, L->ctr, !L->cycles, s) != cudaSuccess ||
+        launch_cand_ball(ca, L->n_chunks, true, s) != cudaSuccess)
+        return TSX_ECUDA;
+    if (L->cycles) {
+        CycleArgs cy{};
+        cy.code = g;
+        cy.l = L->cyc_l;
+        cy.paths = L->paths;
+        cy.count = L->d_cyc_cnt;
+        cy.off = L->d_cyc_off;
+        cy.cands = (int4 *)b.cands;
+        cy.ctr = L->ctr;
+        if (launch_cand_cycle(cy, false, s) != cudaSuccess ||
+            launch_scan(L->d_cyc_cnt, g.n_rep, L->d_cyc_off, L->d_chunk_off + L->n_chunks, L->ctr, true, s) !=
+                cudaSuccess ||
+            launch_cand_cycle(cy, true, s) != cudaSuccess)
+            return TSX_ECUDA;
+    }
+    return record(L, 1, s);
+}
+
+static int enqueue_decode(tsx_ts_list *L, cudaStream_t s) {
+    const tsx_enum_params &p = L->p;
+    if (!L->n_dchunks) {
+        if (launch_decode(L->code->d, L->dp, L->b, p.warps_per_cta, 0, p.ctas_per_sm, L->grid_sms,
+                          p.kernel == 1 ? 1 : 0, s) != cudaSuccess)
+            return TSX_ECUDA;
+        return TSX_OK;
+    }
+    // one launch per chunk: between launches the SMs can go to other streams
+    for (long long k = 0; k < L->n_dchunks; k++) {
+        EnumBuffers bk = L->b;
+        bk.cand_begin = p.cand_begin + k * L->dchunk;
+        bk.cand_end = std::min<long long>(bk.cand_begin + L->dchunk, L->range_end);
+        bk.queue = L->d_queues + k;
+        if (launch_decode(L->code->d, L->dp, bk, p.warps_per_cta, 0, p.ctas_per_sm, L->grid_sms,
+                          p.kernel == 1 ? 1 : 0, s) != cudaSuccess)
+            return TSX_ECUDA;
+    }
+    return TSX_OK;
+}
+
+// sieve, classification, dedupe, compaction
+static int enqueue_back(tsx_ts_list *L, cudaStream_t s) {
+    if (record(L, 2, s) != TSX_OK) return TSX_ECUDA;
+    if (launch_sieve(L->code->d, L->b, L->p.decoder, L->grid_sms, s) != cudaSuccess) return TSX_ECUDA;
+    if (record(L, 3, s) != TSX_OK) return TSX_ECUDA;
+    if (launch_compact(L->b, L->n_rec, L->ts_off, L->ts_count, L->ts_thr, L->slot_map, s) != cudaSuccess)
+        return TSX_ECUDA;
+    return record(L, 4, s);
+}
+
+extern "C" int enumerate_ts(tsx_code *code, const tsx_enum_params *params, void *stream, tsx_ts_list **out) {
+    if (!code || !params || !out) return TSX_EINVAL;
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    tsx_ts_list *L = nullptr;
+    int st = prepare_list(code, params, s, true, &L);
+    if (st != TSX_OK) return st;
+    if ((st = enqueue_front(L, s)) != TSX_OK || (st = enqueue_decode(L, s)) != TSX_OK ||
+        (st = enqueue_back(L, s)) != TSX_OK) {
+        release(L);
+        delete L;
+        return st;
+    }
+    *out = L;
+    return TSX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// tile autotuner: times the decode on a prefix of the candidate list for each
+// admissible (warps per codeword group, message storage) and keeps the fastest
+// ---------------------------------------------------------------------------
+extern "C" int tune_tile(tsx_code *code, const tsx_enum_params *params, void *stream, tsx_enum_params *tuned,
+                         float *ms_best) {
+    if (!code || !params || !tuned) return TSX_EINVAL;
+    int st = check_params(*params);
+    if (st != TSX_OK) return st;
+    *tuned = *params;
+    if (ms_best) *ms_best = -1.0f;
+    if (params->decoder == TSX_DEC_SPA_F32 || params->kernel == 1) return TSX_OK;  // nothing to choose
+    const DevCode &g = code->d;
+    std::vector<int> decs{params->decoder};
+    // int8 storage is exact when every check-to-variable message fits in 8 bits
+    if (params->decoder == TSX_DEC_NMS_I16 && params->sat <= 169) decs.push_back(TSX_DEC_NMS_I8);
+    int work = std::min(g.m, g.n);
+    if (g.kind == TSX_CODE_QC) work = std::min(work, g.Z);
+    std::vector<int> Gs{1};
+    for (int G = 2; G <= 8 && G * 32 <= std::max(32, work); G *= 2) Gs.push_back(G);
+    tsx_enum_params t = *params;
+    t.record_candidates = 0;
+    t.cand_begin = 0;
+    t.cand_end = (long long)code->num_sms * 256;
+    t.ctas_per_sm = 0;
+    float best = -1.0f;
+    bool warm = false;
+    for (int dec : decs)
+        for (int G : Gs) {
+            t.decoder = dec;
+            t.warps_per_cta = G;
+            t.kernel = 0;
+            for (int rep = warm ? 1 : 0; rep < 2; rep++) {
+                tsx_ts_list *L = nullptr;
+                st = enumerate_ts(code, &t, stream, &L);
+                if (st == TSX_EUNSUPPORTED) break;
+                if (st != TSX_OK) return st;
+                tsx_enum_stats es;
+                st = ts_list_stats(L, &es);
+                free_ts_list(L);
+                if (st != TSX_OK) return st;
+                warm = true;
+                if (rep == 1 && (best < 0.0f || es.ms_decode < best)) {
+                    best = es.ms_decode;
+                    tuned->decoder = dec;
+                    tuned->warps_per_cta = G;
+                }
+            }
+        }
+    if (ms_best) *ms_best = best;
+    return TSX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches: several codes, one multi-code decode launch
+// ---------------------------------------------------------------------------
+struct tsx_batch {
+    std::vector<tsx_ts_list *> lists;
+    BatchArgs *items = nullptr;  // host copy, passed by value at each launch
+    int n_items = 0;             // codes in the multi-code launch
+    std::vector<bool> own;       // codes decoded by a launch of their own
+    LaunchShape sh{};
+    int variant = 0;
+    bool multi = false;
+};
+
+extern "C" void batch_free(tsx_batch *B) {
+    if (!B) return;
+    for (tsx_ts_list *L : B->lists) free_ts_list(L);
+    delete B->items;
+    delete B;
+}
+
+extern "C" int batch_create(tsx_code *const *codes, const tsx_enum_params *params, int32_t n, void *stream,
+                            tsx_batch **out) {
+    if (!codes || !params || !out || n <= 0) return TSX_EINVAL;
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    tsx_batch *B = new tsx_batch();
+    for (int i = 0; i < n; i++) {
+        if (!codes[i]) { batch_free(B); return TSX_EINVAL; }
+        tsx_ts_list *L = nullptr;
+        const int st = prepare_list(codes[i], &params[i], s, false, &L);
+        if (st != TSX_OK) { batch_free(B); return st; }
+        B->lists.push_back(L);
+    }
+    std::vector<const DevCode *> gs(n);
+    std::vector<DecodeParams> dps(n);
+    std::vector<EnumBuffers> bs(n);
+    std::vector<BatchItem> items(n);
+    std::vector<int> greq(n);
+    bool all_auto = true;
+    for (int i = 0; i < n; i++) {
+        greq[i] = params[i].warps_per_cta;
+        gs[i] = &B->lists[i]->code->d;
+        dps[i] = B->lists[i]->dp;
+        bs[i] = B->lists[i]->b;
+        all_auto = all_auto && params[i].kernel != 1;
+    }
+    if (all_auto && n <= kMaxBatch &&
+        plan_batch(gs.data(), dps.data(), bs.data(), greq.data(), n, codes[0]->num_sms, items.data(), &B->sh,
+                   &B->variant)) {
+        B->items = new BatchArgs();
+        for (int i = 0; i < n; i++) {
+            B->own.push_back(items[i].scalar != 0);
+            if (!items[i].scalar) B->items->it[B->n_items++] = items[i];
+        }
+        B->multi = B->n_items > 0;
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) { batch_free(B); return TSX_ECUDA; }
+    *out = B;
+    return TSX_OK;
+}
+
+extern "C" int batch_run(tsx_batch *B, void *stream) {
+    if (!B) return TSX_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int st;
+    for (tsx_ts_list *L : B->lists)
+        if ((st = enqueue_front(L, s)) != TSX_OK) return st;
+    if (B->multi) {
+        if (launch_batch(*B->items, B->n_items, B->variant, B->sh, s) != cudaSuccess) return TSX_ECUDA;
+        for (size_t i = 0; i < B->lists.size(); i++)
+            if (B->own[i] && (st = enqueue_decode(B->lists[i], s)) != TSX_OK) return st;
+    } else {
+        for (tsx_ts_list *L : B->lists)
+            if ((st = enqueue_decode(L, s)) != TSX_OK) return st;
+    }
+    for (tsx_ts_list *L : B->lists)
+        if ((st = enqueue_back(L, s)) != TSX_OK) return st;
+    return TSX_OK;
+}
+
+extern "C" int batch_size(const tsx_batch *B) { return B ? (int)B->lists.size() : 0; }
+
+extern "C" int batch_multi_launch(const tsx_batch *B) { return B && B->multi ? 1 : 0; }
+
+extern "C" int batch_view(tsx_batch *B, int32_t i, tsx_ts_view *view) {
+    if (!B || i < 0 || i >= (int)B->lists.size()) return TSX_EINVAL;
+    return ts_list_view(B->lists[i], view);
+}
+
+extern "C" int batch_stats(tsx_batch *B, tsx_enum_stats *total) {
+    if (!B || !total) return TSX_EINVAL;
+    memset(total, 0, sizeof(*total));
+    int ret = TSX_OK;
+    for (tsx_ts_list *L : B->lists) {
+        tsx_enum_stats s;
+        const int st = ts_list_stats(L, &s);
+        if (st != TSX_OK && ret == TSX_OK) ret = st;
+        total->n_cand += s.n_cand;
+        total->n_cand_total += s.n_cand_total;
+        total->n_ts += s.n_ts;
+        total->decodes += s.decodes;
+        total->iterations += s.iterations;
+        total->edge_updates += s.edge_updates;
+        total->acyclic += s.acyclic;
+    }
+    return ret;
 }
 
 static int fetch_counters(tsx_ts_list *L, Counters &c) {
@@ -703,3 +962,56 @@ extern "C" void free_ts_list(tsx_ts_list *L) {
     cudaStreamSynchronize(L->st);
     delete L;
 }
+
+// ---------------------------------------------------------------------------
+// hooks of the serving runtime (server.cu)
+// ---------------------------------------------------------------------------
+namespace tsx {
+
+int list_bytes(tsx_code *code, const tsx_enum_params *params, long long dchunk, long long *bytes,
+               long long *cand_bound) {
+    tsx_ts_list *L = nullptr;
+    const int st = prepare_list(code, params, nullptr, false, &L, dchunk, 0, true);
+    if (st != TSX_OK) return st;
+    *bytes = L->bytes;
+    if (cand_bound) *cand_bound = std::max<long long>(0, L->range_end - L->p.cand_begin);
+    delete L;
+    return TSX_OK;
+}
+
+long long list_cand_bound(const tsx_ts_list *L) { return L->range_end - L->p.cand_begin; }
+
+int list_start(tsx_code *code, const tsx_enum_params *params, cudaStream_t s, long long dchunk, int grid_sms,
+               tsx_ts_list **out) {
+    tsx_ts_list *L = nullptr;
+    int st = prepare_list(code, params, s, true, &L, dchunk, grid_sms, false);
+    if (st != TSX_OK) return st;
+    if ((st = enqueue_front(L, s)) != TSX_OK || (st = enqueue_decode(L, s)) != TSX_OK ||
+        (st = enqueue_back(L, s)) != TSX_OK) {
+        release(L);
+        delete L;
+        return st;
+    }
+    *out = L;
+    return TSX_OK;
+}
+
+// After the list's stream has passed its last kernel: copy the results to
+// the host and give the device memory back (stream-ordered).  The list stays
+// valid for ts_list_view(); delete it with list_delete().
+int list_finish(tsx_ts_list *L) {
+    if (!L->fetched) {
+        L->fetch_status = do_fetch(L);
+        L->fetched = true;
+    }
+    release(L);
+    return L->fetch_status;
+}
+
+void list_delete(tsx_ts_list *L) {
+    if (!L) return;
+    release(L);
+    delete L;
+}
+
+}  // namespace tsx

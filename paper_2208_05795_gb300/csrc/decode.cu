@@ -13,6 +13,10 @@ cudaError_t launch_nms8(const DevCode &, const DecodeParams &, const EnumBuffers
 cudaError_t launch_spa(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, cudaStream_t);
 cudaError_t launch_sieve_kernel(const DevCode &, const EnumBuffers &, const LaunchShape &, int is_float,
                                 cudaStream_t);
+cudaError_t launch_batch16(const BatchArgs &, int, bool qc, int dc_max, bool reg6, const LaunchShape &,
+                           cudaStream_t);
+cudaError_t launch_batch8(const BatchArgs &, int, bool qc, int dc_max, bool reg6, const LaunchShape &,
+                          cudaStream_t);
 
 namespace {
 
@@ -58,7 +62,9 @@ SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
     return L;
 }
 
-constexpr int kSmemCta = 227 * 1024;
+// dynamic shared memory of a CTA: 227 KB less 1 KB for the static part (the
+// batch kernel's staged item)
+constexpr int kSmemCta = 226 * 1024;
 
 bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_per_sm, int num_sms,
           LaunchShape *out) {
@@ -111,9 +117,11 @@ bool pair_ok(const DevCode &g, const DecodeParams &dp) {
 
 cudaError_t launch_decode(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, int G, int groups,
                           int ctas_per_sm, int num_sms, int force_scalar, cudaStream_t st) {
-    const bool pair = !force_scalar && pair_ok(g, dp);
     LaunchShape sh;
-    if (!plan(g, dp.decoder, pair ? kLayPair : kLayScalar, G, groups, ctas_per_sm, num_sms, &sh))
+    // the two-codeword kernel where its bounds hold and its layout fits a CTA
+    const bool pair = !force_scalar && pair_ok(g, dp) && plan(g, dp.decoder, kLayPair, G, groups, ctas_per_sm,
+                                                             num_sms, &sh);
+    if (!pair && !plan(g, dp.decoder, kLayScalar, G, groups, ctas_per_sm, num_sms, &sh))
         return cudaErrorInvalidConfiguration;
     switch (dp.decoder) {
         case TSX_DEC_NMS_I16: return launch_nms16(g, dp, b, sh, pair, st);
@@ -126,6 +134,63 @@ cudaError_t launch_sieve(const DevCode &g, const EnumBuffers &b, int decoder, in
     LaunchShape sh;
     if (!plan(g, decoder, kLaySieve, 1, 0, 0, num_sms, &sh)) return cudaErrorInvalidConfiguration;
     return launch_sieve_kernel(g, b, sh, decoder == TSX_DEC_SPA_F32 ? 1 : 0, st);
+}
+
+// variant bits: 1 = QC, 2 = int8 storage, 4 = all check-regular of degree 6,
+// bits 8.. = the largest check degree
+bool plan_batch(const DevCode *const *g, const DecodeParams *dp, const EnumBuffers *b, const int *G_req, int n,
+                int num_sms, BatchItem *items, LaunchShape *common, int *variant) {
+    if (n <= 0) return false;
+    const int kind = g[0]->kind, dec = dp[0].decoder;
+    bool reg6 = true;
+    int dcmax = 1, smem = 0;
+    for (int i = 0; i < n; i++) {
+        if (g[i]->kind != kind || dp[i].decoder != dec || !pair_ok(*g[i], dp[i])) return false;
+        LaunchShape sh;
+        int G, groups;
+        items[i].scalar = 0;
+        if (!plan(*g[i], dec, kLayPair, 1, 1, 0, num_sms, &sh)) {
+            items[i].scalar = 1;  // decoded by a launch of its own
+            continue;
+        }
+        reg6 = reg6 && g[i]->dc_min == 6 && g[i]->dc_max == 6;
+        if (g[i]->dc_max > dcmax) dcmax = g[i]->dc_max;
+        if (G_req && G_req[i] > 0) {
+            // the requested (tuned) group width, as many groups as fit
+            if (!plan(*g[i], dec, kLayPair, G_req[i], 0, 0, num_sms, &sh)) return false;
+            G = sh.G;
+            groups = sh.groups;
+        } else {
+            // the single-code launch's automatic shape
+            if (!plan(*g[i], dec, kLayPair, 0, 0, 0, num_sms, &sh)) return false;
+            G = sh.G;
+            groups = sh.groups;
+        }
+        items[i].g = *g[i];
+        items[i].dp = dp[i];
+        items[i].b = b[i];
+        items[i].lay = sh.lay;
+        items[i].G = G;
+        items[i].groups = groups;
+        const int need = sh.lay.tables_bytes + groups * sh.lay.slot_bytes;
+        if (need > smem) smem = need;
+    }
+    LaunchShape sh{};
+    sh.G = 1;
+    sh.groups = 16;
+    sh.smem_bytes = smem;
+    sh.num_sms = num_sms;
+    sh.per_sm_req = 0;
+    sh.ctas = num_sms;
+    *common = sh;
+    *variant = (kind == TSX_CODE_QC ? 1 : 0) | (dec == TSX_DEC_NMS_I8 ? 2 : 0) | (reg6 ? 4 : 0) | (dcmax << 8);
+    return true;
+}
+
+cudaError_t launch_batch(const BatchArgs &items, int n, int variant, const LaunchShape &sh, cudaStream_t st) {
+    const bool qc = variant & 1, i8 = variant & 2, reg6 = variant & 4;
+    const int dcmax = variant >> 8;
+    return i8 ? launch_batch8(items, n, qc, dcmax, reg6, sh, st) : launch_batch16(items, n, qc, dcmax, reg6, sh, st);
 }
 
 bool plan_is_shape(const DevCode &g, const DecodeParams &dp, LaunchShape *sh, int num_sms) {

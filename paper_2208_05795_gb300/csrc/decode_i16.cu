@@ -7,4 +7,8 @@ cudaError_t launch_nms16(const DevCode &g, const DecodeParams &dp, const EnumBuf
     if (pair) return launch_pair<false>(g, dp, b, sh, st);
     return launch_scalar<DecNms16>(g, dp, b, sh, st);
 }
+cudaError_t launch_batch16(const BatchArgs &items, int n, bool qc, int dc_max, bool reg6, const LaunchShape &sh,
+                           cudaStream_t st) {
+    return launch_batch_t<false>(items, n, qc, dc_max, reg6, sh, st);
+}
 }  // namespace tsx

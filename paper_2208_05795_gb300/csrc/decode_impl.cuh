@@ -726,7 +726,8 @@ __device__ unsigned long long key_hash(const uint16_t *key, int a, int lane) {
 }
 
 // Insert / find the key; returns the table slot, -1 on a full table, -2 on
-// a pool overflow.  Warp-collective.
+// a pool overflow.  Warp-collective.  The header's flags word ends as the OR
+// of the flags of every insert of the key (independent of their order).
 __device__ long long ts_insert(const EnumBuffers &b, const uint16_t *key, int a, int bb, int orbit,
                                int flags, int lane) {
     const unsigned long long h = key_hash(key, a, lane);
@@ -770,7 +771,11 @@ __device__ long long ts_insert(const EnumBuffers &b, const uint16_t *key, int a,
             bool eq = __ldcg(&b.pool[off]) == a;
             if (eq)
                 for (int i = lane; i < a && eq; i += 32) eq = __ldcg(&b.pool[off + kPoolHdr + i]) == (int)key[i];
-            if (__all_sync(0xffffffffu, eq)) return (long long)slot;
+            if (__all_sync(0xffffffffu, eq)) {
+                // the sieve bits of a set are the union over every candidate that reached it
+                if (lane == 0) atomicOr(&b.pool[off + 3], flags);
+                return (long long)slot;
+            }
         }
         slot = (slot + 1) & b.cap_mask;
     }
@@ -782,17 +787,13 @@ __device__ long long ts_insert(const EnumBuffers &b, const uint16_t *key, int a,
 // the kernel
 // ---------------------------------------------------------------------------
 template <class Dec, int DCMAX, bool QC>
-__global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, EnumBuffers b,
-                                                    SlotLayout lay, int G) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void scalar_run(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b,
+                                           const SlotLayout &lay, int G, const SGraph &sg, unsigned char *smem,
+                                           int grp) {
     using lv = typename Dec::lv;
     using post = typename Dec::post;
     using msg = typename Dec::msg;
-    const SGraph sg = load_tables(g, smem);
-    __syncthreads();
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = warp / G;
     unsigned char *slot = smem + lay.tables_bytes + grp * lay.slot_bytes;
     Misc *misc = (Misc *)(slot + lay.misc_off);
     Grp gp;
@@ -819,7 +820,7 @@ __global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, E
     else Lbase = (lv)clampi(dp.base_llr, -dp.sat, dp.sat);
 
     while (true) {
-        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(&b.ctr->next_cand, 1ull);
+        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(b.queue, 1ull);
         gp.sync();
         const long long idx = b.cand_begin + misc->bcast[0];
         gp.sync();
@@ -888,7 +889,7 @@ __global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, E
 
         // records and the failing decode's x* for the sieve kernel
         gp.sync();
-        const long long o = idx - b.cand_begin;
+        const long long o = idx - b.rec_base;
         if (failed) {
             uint32_t *dst = b.xstar + o * (long long)b.nw;
             for (int w = gp.gt; w < b.nw; w += gp.T) dst[w] = xkeep[w];
@@ -908,6 +909,15 @@ __global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, E
         atomicAdd(&b.ctr->iterations, (unsigned long long)my_it);
         atomicAdd(&b.ctr->edge_updates, (unsigned long long)my_eu);
     }
+}
+
+template <class Dec, int DCMAX, bool QC>
+__global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, EnumBuffers b,
+                                                    SlotLayout lay, int G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SGraph sg = load_tables(g, smem);
+    __syncthreads();
+    scalar_run<Dec, DCMAX, QC>(g, dp, b, lay, G, sg, smem, (threadIdx.x >> 5) / G);
 }
 
 // ---------------------------------------------------------------------------

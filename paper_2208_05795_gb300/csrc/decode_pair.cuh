@@ -103,6 +103,31 @@ struct PairDecoder {
     template <class PV, class RE>
     __device__ __forceinline__ int check_node(int deg, unsigned km, unsigned kb, bool writeR, const unsigned char *Pc,
                                               unsigned char *Pn, PV pv, RE re) const {
+        if constexpr (DC <= 8) return check_node_regs(deg, km, kb, writeR, Pc, Pn, pv, re);
+        else return check_node_twopass(deg, km, kb, writeR, Pc, Pn, pv, re);
+    }
+
+    // extrinsic value q'' = clamp(q) + beta and magnitude |q| + beta of one edge
+    __device__ __forceinline__ void edge_q(unsigned x, unsigned y, unsigned &q, unsigned &a) const {
+        q = vminu2(vmaxu2(x - y, pc.LO2), pc.HI2) + pc.B2;
+        a = vmaxu2(q, (~q) + 0x00010001u);
+    }
+
+    // the new message of an edge from its q'', |q|, the check's min1, the
+    // two output magnitudes and the sign parity of all its edges
+    __device__ __forceinline__ unsigned edge_out(unsigned q, unsigned a, unsigned m1, unsigned o1, unsigned o2,
+                                                 unsigned sxk) const {
+        const unsigned neg = spread15(sxk ^ q);                  // 0xFFFF: others' sign product < 0
+        const unsigned ne = spread15(a - m1 + 0x7FFF7FFFu);      // 0xFFFF: |q_p| != min1
+        const unsigned mag = (o1 & ne) | (o2 & ~ne);
+        const unsigned pos = pc.B2 + mag, ng = pc.B2 - mag;
+        return (ng & neg) | (pos & ~neg);
+    }
+
+    // small degree: the edges' q and |q| stay in registers between the passes
+    template <class PV, class RE>
+    __device__ __forceinline__ int check_node_regs(int deg, unsigned km, unsigned kb, bool writeR,
+                                                   const unsigned char *Pc, unsigned char *Pn, PV pv, RE re) const {
         unsigned sp = 0, sx = 0, m1 = pc.BS2, m2 = pc.BS2;
         unsigned qs[DC], as_[DC];
         int po[DC];
@@ -113,10 +138,9 @@ struct PairDecoder {
                 const unsigned x = *(const unsigned *)(Pc + po[p]);
                 const unsigned y = (ldR(re(p)) & km) | kb;
                 sp ^= x;
-                unsigned q = x - y;
-                q = vminu2(vmaxu2(q, pc.LO2), pc.HI2) + pc.B2;
+                unsigned q, a;
+                edge_q(x, y, q, a);
                 sx ^= q;
-                const unsigned a = vmaxu2(q, (~q) + 0x00010001u);
                 m2 = vminu2(m2, vmaxu2(m1, a));
                 m1 = vminu2(m1, a);
                 qs[p] = q;
@@ -133,18 +157,63 @@ struct PairDecoder {
             const unsigned o2 = ((d2 * (unsigned)pc.an) >> pc.as) & pc.amask2;
             // bit 15 of sx ^ q_p = parity of #(q >= 0) over the other edges;
             // negatives among the others = (deg - 1) - that
-            const unsigned kodd = ((deg - 1) & 1) ? 0x80008000u : 0u;
+            const unsigned sxk = sx ^ (((deg - 1) & 1) ? 0x80008000u : 0u);
 #pragma unroll
             for (int p = 0; p < DC; p++) {
                 if (EXACT || p < deg) {
-                    const unsigned neg = spread15(sx ^ qs[p] ^ kodd);        // 0xFFFF: others' sign product < 0
-                    const unsigned ne = spread15(as_[p] - m1 + 0x7FFF7FFFu);  // 0xFFFF: |q_p| != min1
-                    const unsigned mag = (o1 & ne) | (o2 & ~ne);
-                    const unsigned pos = pc.B2 + mag, ng = pc.B2 - mag;
-                    const unsigned rn = (ng & neg) | (pos & ~neg);
+                    const unsigned rn = edge_out(qs[p], as_[p], m1, o1, o2, sxk);
                     stR(re(p), rn);
                     red_add(Pn + po[p], rn);
                 }
+            }
+        }
+        return (int)(((unsat >> 15) & 1u) | ((unsat >> 30) & 2u));
+    }
+
+    // large degree: the first pass leaves each edge's q'' in its message slot
+    // (16-bit storage: a slot holds both halves' q''), the second reads it
+    // back; with 8-bit storage the second pass reloads P and recomputes q
+    template <class PV, class RE>
+    __device__ __forceinline__ int check_node_twopass(int deg, unsigned km, unsigned kb, bool writeR,
+                                                      const unsigned char *Pc, unsigned char *Pn, PV pv,
+                                                      RE re) const {
+        unsigned sp = 0, sx = 0, m1 = pc.BS2, m2 = pc.BS2;
+#pragma unroll 4
+        for (int p = 0; p < deg; p++) {
+            const int ro = re(p);
+            const unsigned x = *(const unsigned *)(Pc + pv(p));
+            const unsigned y = (ldR(ro) & km) | kb;
+            sp ^= x;
+            unsigned q, a;
+            edge_q(x, y, q, a);
+            if constexpr (!I8)
+                if (writeR) stR(ro, q);
+            sx ^= q;
+            m2 = vminu2(m2, vmaxu2(m1, a));
+            m1 = vminu2(m1, a);
+        }
+        const unsigned dodd = (deg & 1) ? 0x80008000u : 0u;
+        const unsigned unsat = (sp ^ dodd) & 0x80008000u;
+        if (writeR) {
+            const unsigned d1 = m1 - pc.BETA2, d2 = m2 - pc.BETA2;
+            const unsigned o1 = ((d1 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o2 = ((d2 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned sxk = sx ^ (((deg - 1) & 1) ? 0x80008000u : 0u);
+#pragma unroll 4
+            for (int p = 0; p < deg; p++) {
+                const int po = pv(p), ro = re(p);
+                unsigned q, a;
+                if constexpr (!I8) {
+                    q = ldR(ro);
+                    a = vmaxu2(q, (~q) + 0x00010001u);
+                } else {
+                    const unsigned x = *(const unsigned *)(Pc + po);
+                    const unsigned y = (ldR(ro) & km) | kb;
+                    edge_q(x, y, q, a);
+                }
+                const unsigned rn = edge_out(q, a, m1, o1, o2, sxk);
+                stR(ro, rn);
+                red_add(Pn + po, rn);
             }
         }
         return (int)(((unsat >> 15) & 1u) | ((unsat >> 30) & 2u));
@@ -261,14 +330,12 @@ struct PairDecoder {
     }
 };
 
+// The decode loop of one group (G warps, group index grp) over the
+// candidate queue of one code; the code's tables are already in sg.
 template <bool QC, int DC, bool EXACT, bool I8>
-__global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay,
-                                                   int G) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const SGraph sg = load_tables(g, smem);
-    __syncthreads();
+__device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const SlotLayout &lay,
+                         int G, const SGraph &sg, unsigned char *smem, int grp) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = warp / G;
     unsigned char *slot = smem + lay.tables_bytes + grp * lay.slot_bytes;
     Misc *misc = (Misc *)(slot + lay.misc_off);
     Grp gp;
@@ -308,7 +375,7 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
     Half H[2];
 
     auto fetch = [&](Half &h) {
-        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(&b.ctr->next_cand, 1ull);
+        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(b.queue, 1ull);
         gp.sync();
         const long long idx = b.cand_begin + misc->bcast[0];
         gp.sync();
@@ -332,7 +399,7 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
     // finish the candidate of half hh (records, x* to global) and fetch the next
     auto finish = [&](Half &h, int hh) {
         gp.sync();
-        const long long o = h.idx - b.cand_begin;
+        const long long o = h.idx - b.rec_base;
         if (h.failed) {
             const uint32_t *src = xb + (2 * hh + (h.cur ^ 1)) * xstride;
             uint32_t *dst = b.xstar + o * (long long)b.nw;
@@ -479,6 +546,35 @@ __global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, E
     }
 }
 
+template <bool QC, int DC, bool EXACT, bool I8>
+__global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay,
+                                                   int G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SGraph sg = load_tables(g, smem);
+    __syncthreads();
+    pair_run<QC, DC, EXACT, I8>(g, dp, b, lay, G, sg, smem, (threadIdx.x >> 5) / G);
+}
+
+// One persistent launch over several codes: every CTA works through the
+// codes in order, each with its own tables, slot layout and group size,
+// taking candidates from that code's queue until it is empty (CTAs move
+// on independently, so no code waits for the slowest CTA of another).
+// The items are a __grid_constant__ kernel parameter: the decoders read
+// each code's description from the constant bank, as the single-code kernel
+// does, instead of holding it in registers.
+template <bool QC, int DC, bool EXACT, bool I8>
+__global__ void __launch_bounds__(512) batch_kernel(const __grid_constant__ BatchArgs args, int n_items) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    for (int c = 0; c < n_items; c++) {
+        const BatchItem &it = args.it[c];
+        const SGraph sg = load_tables(it.g, smem);
+        __syncthreads();
+        const int grp = (threadIdx.x >> 5) / it.G;
+        if (grp < it.groups) pair_run<QC, DC, EXACT, I8>(it.g, it.dp, it.b, it.lay, it.G, sg, smem, grp);
+        __syncthreads();
+    }
+}
+
 template <bool I8>
 cudaError_t launch_pair(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const LaunchShape &sh,
                         cudaStream_t st) {
@@ -492,6 +588,19 @@ cudaError_t launch_pair(const DevCode &g, const DecodeParams &dp, const EnumBuff
                   : launch_persistent(pair_kernel<false, 8, false, I8>, sh, st, g, dp, b, sh.lay, sh.G);
     return qc ? launch_persistent(pair_kernel<true, 32, false, I8>, sh, st, g, dp, b, sh.lay, sh.G)
               : launch_persistent(pair_kernel<false, 32, false, I8>, sh, st, g, dp, b, sh.lay, sh.G);
+}
+
+template <bool I8>
+cudaError_t launch_batch_t(const BatchArgs &items, int n, bool qc, int dc_max, bool reg6, const LaunchShape &sh,
+                           cudaStream_t st) {
+    if (reg6)
+        return qc ? launch_persistent(batch_kernel<true, 6, true, I8>, sh, st, items, n)
+                  : launch_persistent(batch_kernel<false, 6, true, I8>, sh, st, items, n);
+    if (dc_max <= 8)
+        return qc ? launch_persistent(batch_kernel<true, 8, false, I8>, sh, st, items, n)
+                  : launch_persistent(batch_kernel<false, 8, false, I8>, sh, st, items, n);
+    return qc ? launch_persistent(batch_kernel<true, 32, false, I8>, sh, st, items, n)
+              : launch_persistent(batch_kernel<false, 32, false, I8>, sh, st, items, n);
 }
 
 }  // namespace

@@ -132,6 +132,7 @@ struct IsArgs {
     unsigned char *fail_out;  // [nsamp] or null
     double *logw_out;         // [nsamp] or null
     Counters *ctr;
+    unsigned long long *queue;  // work-queue word of this launch (samples s0 + i, i < nsamp)
 };
 
 // ---------------------------------------------------------------------------
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsA
     int pcur = 0;
 
     auto fetch = [&](int hh) {
-        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(&ia.ctr->next_cand, 1ull);
+        if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(ia.queue, 1ull);
         gp.sync();
         const long long i = misc->bcast[0];
         gp.sync();
@@ -336,9 +337,28 @@ extern "C" void is_params_default(tsx_is_params *p) {
     p->alpha_shift = 2;
 }
 
-extern "C" int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p,
-                               void *stream, tsx_is_result *out, uint8_t *fail_out, double *logw_out) {
-    if (!code || !p || !out || a < 0 || (a > 0 && !ts_vars)) return TSX_EINVAL;
+// ---------------------------------------------------------------------------
+// jobs: validation and sizing, enqueue, collection
+// ---------------------------------------------------------------------------
+namespace tsx {
+
+struct IsJob {
+    DevCode g;
+    DecodeParams dp{};
+    LaunchShape sh{};
+    IsArgs ia{};
+    long long N = 0, chunk = 0, n_chunks = 0;
+    int nb = 0, grid_sms = 0;
+    std::vector<int> Ts;
+    size_t off_p = 0, off_o = 0, off_q = 0, total = 0;
+    unsigned char *B = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+static int is_plan(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p, long long chunk,
+                   IsJob &J) {
+    if (!code || !p || a < 0 || (a > 0 && !ts_vars)) return TSX_EINVAL;
     if (p->n_samples < 0 || p->sample_begin < 0 || p->K < 0 || p->K > 100000) return TSX_EINVAL;
     if (p->sat < 1 || p->sat > 8191 || p->alpha_shift < 0 || p->alpha_shift > 15 || p->alpha_num < 1 ||
         p->alpha_num > (1 << p->alpha_shift))
@@ -348,24 +368,23 @@ extern "C" int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a
         if (ts_vars[t] < 0 || ts_vars[t] >= g.n) return TSX_EINVAL;
     const double rate = p->rate > 0.0 ? p->rate : 1.0 - (double)g.m / (double)g.n;
     if (!(rate > 0.0) || !(p->ebn0_db > -100.0 && p->ebn0_db < 100.0)) return TSX_EINVAL;
-    DecodeParams dp{};
-    dp.decoder = TSX_DEC_NMS_I16;
-    dp.K = p->K;
-    dp.sat = p->sat;
-    dp.alpha_num = p->alpha_num;
-    dp.alpha_shift = p->alpha_shift;
-    dp.base_llr = 1;
-    LaunchShape sh;
-    if (!plan_is_shape(g, dp, &sh, code_num_sms(code))) return TSX_EUNSUPPORTED;
-    memset(out, 0, sizeof(*out));
+    J.g = g;
+    J.dp.decoder = TSX_DEC_NMS_I16;
+    J.dp.K = p->K;
+    J.dp.sat = p->sat;
+    J.dp.alpha_num = p->alpha_num;
+    J.dp.alpha_shift = p->alpha_shift;
+    J.dp.base_llr = 1;
+    if (!plan_is_shape(g, J.dp, &J.sh, code_num_sms(code))) return TSX_EUNSUPPORTED;
     const long long N = p->n_samples;
-    out->n_samples = N;
-    if (N == 0) return TSX_OK;
+    J.N = N;
+    J.chunk = chunk > 0 && chunk < N ? chunk : N;
+    J.n_chunks = N > 0 ? (N + J.chunk - 1) / J.chunk : 0;
 
     // sigma^2 = 1 / (2 R Eb/N0); float constants and log-weight coefficients
     const double ebn0 = pow(10.0, p->ebn0_db / 10.0);
     const double s2 = 1.0 / (2.0 * rate * ebn0);
-    IsArgs ia{};
+    IsArgs &ia = J.ia;
     ia.job = p->job_key;
     ia.s0 = (unsigned long long)p->sample_begin;
     ia.nsamp = N;
@@ -374,83 +393,153 @@ extern "C" int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a
     ia.cq = (float)(16.0 / s2);
     ia.A = p->mu / s2;
     ia.Bc = p->mu * p->mu / (2.0 * s2);
-    ia.a = a;
+    J.Ts.assign(ts_vars, ts_vars + a);
+    std::sort(J.Ts.begin(), J.Ts.end());
+    J.Ts.erase(std::unique(J.Ts.begin(), J.Ts.end()), J.Ts.end());
+    ia.a = (int)J.Ts.size();
 
-    cudaStream_t s = (cudaStream_t)stream;
-    std::vector<int> Ts(ts_vars, ts_vars + a);
-    std::sort(Ts.begin(), Ts.end());
-    Ts.erase(std::unique(Ts.begin(), Ts.end()), Ts.end());
-    a = (int32_t)Ts.size();
-    ia.a = a;
-    const int nb = (int)((N + kRedChunk - 1) / kRedChunk);
+    // one device block: T | fail*w | fail | log w | partial sums | sums | counters | queues
+    J.nb = (int)((N + kRedChunk - 1) / kRedChunk);
+    auto r256 = [](size_t x) { return (x + 255) / 256 * 256; };
+    const size_t off_w = 256 + r256((size_t)ia.a * 4);
+    const size_t off_f = off_w + r256((size_t)N * 8);
+    const size_t off_l = off_f + r256((size_t)N);
+    J.off_p = off_l + r256((size_t)N * 8);
+    J.off_o = J.off_p + r256((size_t)J.nb * 16);
+    const size_t off_c = J.off_o + 256;
+    J.off_q = off_c + r256(sizeof(Counters));
+    J.total = J.off_q + r256((size_t)std::max<long long>(1, J.n_chunks) * 8);
+    return TSX_OK;
+}
+
+int is_job_bytes(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p, long long chunk,
+                 long long *bytes) {
+    IsJob J;
+    const int st = is_plan(code, ts_vars, a, p, chunk, J);
+    if (st == TSX_OK) *bytes = (long long)J.total;
+    return st;
+}
+
+void is_job_delete(IsJob *J) {
+    if (!J) return;
+    if (J->B) cudaFreeAsync(J->B, J->st);
+    if (J->e0) cudaEventDestroy(J->e0);
+    if (J->e1) cudaEventDestroy(J->e1);
+    delete J;
+}
+
+// Allocates the job's device block and enqueues the sampling launches (one
+// per chunk of samples), the fixed-order reduction and the end event.
+int is_job_start(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p, cudaStream_t s,
+                 long long chunk, int grid_sms, IsJob **out) {
+    *out = nullptr;
+    IsJob *J = new IsJob();
+    int st = is_plan(code, ts_vars, a, p, chunk, *J);
+    if (st != TSX_OK) { delete J; return st; }
+    J->st = s;
+    J->grid_sms = grid_sms > 0 ? std::min(grid_sms, code_num_sms(code)) : code_num_sms(code);
+    J->sh.num_sms = J->grid_sms;
     void *blk = nullptr;
-    const size_t off_T = 0, off_w = 256 + ((size_t)a * 4 + 255) / 256 * 256;
-    const size_t off_f = off_w + ((size_t)N * 8 + 255) / 256 * 256;
-    const size_t off_l = off_f + ((size_t)N + 255) / 256 * 256;
-    const size_t off_p = off_l + ((size_t)N * 8 + 255) / 256 * 256;
-    const size_t off_o = off_p + ((size_t)nb * 16 + 255) / 256 * 256;
-    const size_t off_c = off_o + 256;
-    const size_t total = off_c + 256;
-    if (cudaMallocAsync(&blk, total, s) != cudaSuccess) return TSX_ENOMEM;
-    unsigned char *B = (unsigned char *)blk;
-    ia.T = (const int *)(B + off_T);
-    ia.wfail = (double *)(B + off_w);
-    ia.fail_out = (unsigned char *)(B + off_f);
-    ia.logw_out = (double *)(B + off_l);
-    ia.ctr = (Counters *)(B + off_c);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    int st = TSX_OK;
-    Counters c{};
-    double sums[2] = {0.0, 0.0};
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = TSX_ECUDA;
-    if (st == TSX_OK && a > 0 &&
-        cudaMemcpyAsync((void *)ia.T, Ts.data(), sizeof(int) * a, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        st = TSX_ECUDA;
-    if (st == TSX_OK && cudaMemsetAsync(ia.ctr, 0, sizeof(Counters), s) != cudaSuccess) st = TSX_ECUDA;
-    if (st == TSX_OK && cudaEventRecord(e0, s) != cudaSuccess) st = TSX_ECUDA;
-    if (st == TSX_OK) {
-        const bool qc = g.kind == TSX_CODE_QC;
-        const bool reg6 = g.dc_min == 6 && g.dc_max == 6;
+    if (cudaMallocAsync(&blk, J->total, s) != cudaSuccess) {
+        cudaGetLastError();
+        delete J;
+        return TSX_ENOMEM;
+    }
+    J->B = (unsigned char *)blk;
+    IsArgs &ia = J->ia;
+    ia.T = (const int *)J->B;
+    const size_t off_w = 256 + (((size_t)ia.a * 4 + 255) / 256 * 256);
+    ia.wfail = (double *)(J->B + off_w);
+    ia.fail_out = (unsigned char *)(J->B + off_w + ((size_t)J->N * 8 + 255) / 256 * 256);
+    ia.logw_out = (double *)((unsigned char *)ia.fail_out + ((size_t)J->N + 255) / 256 * 256);
+    ia.ctr = (Counters *)(J->B + J->off_o + 256);
+    unsigned long long *queues = (unsigned long long *)(J->B + J->off_q);
+    auto bail = [&](int code_) { is_job_delete(J); return code_; };
+    if (cudaEventCreate(&J->e0) != cudaSuccess || cudaEventCreate(&J->e1) != cudaSuccess) return bail(TSX_ECUDA);
+    if (ia.a > 0 &&
+        cudaMemcpyAsync((void *)ia.T, J->Ts.data(), sizeof(int) * ia.a, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return bail(TSX_ECUDA);
+    if (cudaMemsetAsync(ia.ctr, 0, sizeof(Counters), s) != cudaSuccess ||
+        cudaMemsetAsync(queues, 0, 8 * (size_t)std::max<long long>(1, J->n_chunks), s) != cudaSuccess ||
+        cudaEventRecord(J->e0, s) != cudaSuccess)
+        return bail(TSX_ECUDA);
+    const DevCode &g = J->g;
+    const bool qc = g.kind == TSX_CODE_QC;
+    const bool reg6 = g.dc_min == 6 && g.dc_max == 6;
+    for (long long k = 0; k < J->n_chunks; k++) {
+        IsArgs ik = ia;
+        const long long b0 = k * J->chunk;
+        ik.s0 = ia.s0 + (unsigned long long)b0;
+        ik.nsamp = std::min<long long>(J->chunk, J->N - b0);
+        ik.wfail = ia.wfail + b0;
+        ik.fail_out = ia.fail_out + b0;
+        ik.logw_out = ia.logw_out + b0;
+        ik.queue = queues + k;
+        const LaunchShape &sh = J->sh;
         cudaError_t e;
         if (reg6)
-            e = qc ? launch_persistent(is_kernel<true, 6, true>, sh, s, g, dp, ia, sh.lay, sh.G)
-                   : launch_persistent(is_kernel<false, 6, true>, sh, s, g, dp, ia, sh.lay, sh.G);
+            e = qc ? launch_persistent(is_kernel<true, 6, true>, sh, s, g, J->dp, ik, sh.lay, sh.G)
+                   : launch_persistent(is_kernel<false, 6, true>, sh, s, g, J->dp, ik, sh.lay, sh.G);
         else if (g.dc_max <= 8)
-            e = qc ? launch_persistent(is_kernel<true, 8, false>, sh, s, g, dp, ia, sh.lay, sh.G)
-                   : launch_persistent(is_kernel<false, 8, false>, sh, s, g, dp, ia, sh.lay, sh.G);
+            e = qc ? launch_persistent(is_kernel<true, 8, false>, sh, s, g, J->dp, ik, sh.lay, sh.G)
+                   : launch_persistent(is_kernel<false, 8, false>, sh, s, g, J->dp, ik, sh.lay, sh.G);
         else
-            e = qc ? launch_persistent(is_kernel<true, 32, false>, sh, s, g, dp, ia, sh.lay, sh.G)
-                   : launch_persistent(is_kernel<false, 32, false>, sh, s, g, dp, ia, sh.lay, sh.G);
-        if (e != cudaSuccess) st = TSX_ECUDA;
+            e = qc ? launch_persistent(is_kernel<true, 32, false>, sh, s, g, J->dp, ik, sh.lay, sh.G)
+                   : launch_persistent(is_kernel<false, 32, false>, sh, s, g, J->dp, ik, sh.lay, sh.G);
+        if (e != cudaSuccess) return bail(TSX_ECUDA);
     }
-    if (st == TSX_OK) {
-        reduce_kernel<<<nb, kRedBlock, 0, s>>>(ia.wfail, N, (double *)(B + off_p));
-        finish_kernel<<<1, 32, 0, s>>>((const double *)(B + off_p), nb, (double *)(B + off_o));
-        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess) st = TSX_ECUDA;
+    if (J->N > 0) {
+        reduce_kernel<<<J->nb, kRedBlock, 0, s>>>(ia.wfail, J->N, (double *)(J->B + J->off_p));
+        finish_kernel<<<1, 32, 0, s>>>((const double *)(J->B + J->off_p), J->nb, (double *)(J->B + J->off_o));
+        if (cudaGetLastError() != cudaSuccess) return bail(TSX_ECUDA);
     }
-    if (st == TSX_OK &&
-        (cudaMemcpyAsync(sums, B + off_o, sizeof(sums), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaMemcpyAsync(&c, ia.ctr, sizeof(c), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         (fail_out && cudaMemcpyAsync(fail_out, ia.fail_out, N, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
-         (logw_out && cudaMemcpyAsync(logw_out, ia.logw_out, N * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess) ||
-         cudaStreamSynchronize(s) != cudaSuccess))
-        st = TSX_ECUDA;
-    if (st == TSX_OK) {
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        out->sum_w = sums[0];
-        out->sum_w2 = sums[1];
-        out->fer = sums[0] / (double)N;
-        out->var = (sums[1] / (double)N - out->fer * out->fer) / (double)N;
-        out->n_fail = (int64_t)c.n_fail;
-        out->decodes = (int64_t)c.decodes;
-        out->iterations = (int64_t)c.iterations;
-        out->edge_updates = (int64_t)c.edge_updates;
-        out->ms = ms;
-    }
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaFreeAsync(blk, s);
-    cudaStreamSynchronize(s);
+    if (cudaEventRecord(J->e1, s) != cudaSuccess) return bail(TSX_ECUDA);
+    *out = J;
+    return TSX_OK;
+}
+
+// After the job's stream has passed its end event: results to the host; the
+// device block is given back (stream-ordered).
+int is_job_finish(IsJob *J, tsx_is_result *out, uint8_t *fail_out, double *logw_out) {
+    memset(out, 0, sizeof(*out));
+    out->n_samples = J->N;
+    if (J->N == 0) return TSX_OK;
+    double sums[2] = {0.0, 0.0};
+    Counters c{};
+    if (cudaEventSynchronize(J->e1) != cudaSuccess ||
+        cudaMemcpy(sums, J->B + J->off_o, sizeof(sums), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&c, J->ia.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (fail_out && cudaMemcpy(fail_out, J->ia.fail_out, J->N, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (logw_out && cudaMemcpy(logw_out, J->ia.logw_out, J->N * 8, cudaMemcpyDeviceToHost) != cudaSuccess))
+        return TSX_ECUDA;
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, J->e0, J->e1);
+    const double N = (double)J->N;
+    out->sum_w = sums[0];
+    out->sum_w2 = sums[1];
+    out->fer = sums[0] / N;
+    out->var = (sums[1] / N - out->fer * out->fer) / N;
+    out->n_fail = (int64_t)c.n_fail;
+    out->decodes = (int64_t)c.decodes;
+    out->iterations = (int64_t)c.iterations;
+    out->edge_updates = (int64_t)c.edge_updates;
+    out->ms = ms;
+    cudaFreeAsync(J->B, J->st);
+    J->B = nullptr;
+    return TSX_OK;
+}
+
+}  // namespace tsx
+
+extern "C" int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p,
+                               void *stream, tsx_is_result *out, uint8_t *fail_out, double *logw_out) {
+    if (!code || !p || !out) return TSX_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    IsJob *J = nullptr;
+    int st = is_job_start(code, ts_vars, a, p, s, 0, 0, &J);
+    if (st != TSX_OK) return st;
+    st = is_job_finish(J, out, fail_out, logw_out);
+    is_job_delete(J);
+    if (cudaStreamSynchronize(s) != cudaSuccess && st == TSX_OK) st = TSX_ECUDA;
     return st;
 }

@@ -53,6 +53,34 @@ struct LaunchShape {
     SlotLayout lay;
 };
 
+// One code of a multi-code decode launch.
+struct BatchItem {
+    DevCode g;
+    DecodeParams dp;
+    EnumBuffers b;
+    SlotLayout lay;
+    int G, groups;
+    int scalar;  // 1: not in the multi-code launch (its pair layout does not fit a CTA)
+};
+
+// All items of a multi-code launch, passed by value as one kernel parameter
+// (kernel parameters may take up to 32 KB).
+constexpr int kMaxBatch = 64;
+struct BatchArgs {
+    BatchItem it[kMaxBatch];
+};
+static_assert(sizeof(BatchArgs) + 64 <= 32764, "batch kernel parameters above 32 KB");
+
+// Plans a multi-code launch of the two-codewords-per-lane kernel (fills
+// items[] on the host and the common shape over the items that take part);
+// a code whose pair layout does not fit a CTA's shared memory gets
+// scalar = 1 and is left to a launch of its own.  False if the codes cannot
+// share one kernel (kind, decoder or 16-bit bounds differ).
+bool plan_batch(const DevCode *const *g, const DecodeParams *dp, const EnumBuffers *b, const int *G_req, int n,
+                int num_sms, BatchItem *items, LaunchShape *common, int *variant);
+// Launches it over the device copy of items[].
+cudaError_t launch_batch(const BatchArgs &items, int n, int variant, const LaunchShape &sh, cudaStream_t st);
+
 // Runs the impulse decodes with bisection over the candidates of b and
 // writes the per-candidate records and x* of failing candidates.  NMS
 // decoders use the two-codeword kernel where its 16-bit bias bounds hold
@@ -84,5 +112,28 @@ int enum_params_to_decode(const tsx_enum_params *p, DecodeParams *dp);
 // candidates' slots as indices.
 cudaError_t launch_compact(const EnumBuffers &b, long long n_rec, int *ts_off, int *ts_count,
                            int *ts_thr, int *slot_map, cudaStream_t st);
+
+// ---- serving runtime hooks ------------------------------------------------
+// enumeration lists (api.cu): device bytes and candidate bound of a list, start (allocate and
+// enqueue everything), finish (after the stream passed: results to the host,
+// device memory back), delete.  dchunk > 0 splits the decode into launches of
+// dchunk candidates; grid_sms > 0 caps the persistent grids at that many SMs.
+int list_bytes(tsx_code *code, const tsx_enum_params *params, long long dchunk, long long *bytes,
+               long long *cand_bound);
+int list_start(tsx_code *code, const tsx_enum_params *params, cudaStream_t s, long long dchunk, int grid_sms,
+               tsx_ts_list **out);
+long long list_cand_bound(const tsx_ts_list *L);
+int list_finish(tsx_ts_list *L);
+void list_delete(tsx_ts_list *L);
+
+// importance-sampling jobs (isfer.cu), the same protocol; chunk > 0 splits
+// the samples into launches of chunk samples (results do not change).
+struct IsJob;
+int is_job_bytes(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p, long long chunk,
+                 long long *bytes);
+int is_job_start(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *p, cudaStream_t s,
+                 long long chunk, int grid_sms, IsJob **out);
+int is_job_finish(IsJob *J, tsx_is_result *out, uint8_t *fail_out, double *logw_out);
+void is_job_delete(IsJob *J);
 
 }  // namespace tsx

@@ -127,6 +127,8 @@ extern "C" int decode_thresholds_noalloc(const tsx_code *code, const tsx_enum_pa
     b.xstar = (uint32_t *)(sc + off_x);
     b.nw = nw;
     b.ctr = (Counters *)sc;
+    b.queue = &b.ctr->next_cand;
+    b.rec_base = 0;
     if (launch_decode(g, dp, b, params->warps_per_cta, 0, params->ctas_per_sm, code_num_sms(code),
                       params->kernel == 1 ? 1 : 0, s) != cudaSuccess)
         return TSX_ECUDA;

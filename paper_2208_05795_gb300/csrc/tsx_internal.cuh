@@ -53,7 +53,7 @@ struct DevCode {
 
 // Device-wide counters and flags of one enumeration.
 struct Counters {
-    unsigned long long next_cand;   // work queue head (relative to cand_begin)
+    unsigned long long next_cand;   // work queue head of a single-launch decode
     unsigned long long decodes;
     unsigned long long iterations;
     unsigned long long edge_updates;
@@ -94,7 +94,13 @@ struct EnumBuffers {
     long long cand_begin;     // first candidate to decode
     long long cand_end;       // one past the last (clamped to the total on device)
     int record;               // (unused on the device: records are always kept)
-    // per-candidate outputs, indexed by (candidate - cand_begin)
+    // decode work queue: the next candidate is cand_begin + atomicAdd(*queue, 1);
+    // records are indexed by (candidate - rec_base).  A list decoded in one
+    // launch has queue = &ctr->next_cand and rec_base = cand_begin; a list
+    // decoded in chunks gives every chunk launch its own queue word and range.
+    unsigned long long *queue;
+    long long rec_base;
+    // per-candidate outputs, indexed by (candidate - rec_base)
     int *c_thr;
     float *c_thr_f;
     int *c_slot;
