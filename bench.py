@@ -11,6 +11,7 @@ device tables) are resident when the timed region starts; L2 is flushed
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
   python bench.py --workload batch32 [--tune]   # 32 codes, one graph-replayed batch
   python bench.py --workload serve [--jobs N --load F]   # Poisson job stream, p50/p99
+  python bench.py --workload isfer [--samples N]          # importance-sampling FER job
 
 The batch32 workload enumerates the 32 QC codes of uneven sizes (4 x 16 to
 4 x 32 bases, Z 64 to 384) together: per-code candidate kernels and sieves,
@@ -41,6 +42,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
+from paper_2208_05795_gb300.shard import reduce_time_and_work  # noqa: E402
 
 # integer operations the min-sum edge update needs at minimum: |q|, two
 # compare-selects for min1/min2, argmin select, sign xor, output select,
@@ -60,7 +62,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="peg1008", choices=sorted(synth.WORKLOADS) + ["batch32", "serve"])
+    ap.add_argument("--workload", default="peg1008",
+                    choices=sorted(synth.WORKLOADS) + ["batch32", "serve", "isfer"])
+    ap.add_argument("--samples", type=int, default=1_000_000, help="isfer: samples per step")
+    ap.add_argument("--batch-seeds", default="", help="batch32: comma-separated code seeds instead of 100..131 "
+                                                      "(a bounded case for profiling)")
     ap.add_argument("--jobs", type=int, default=120, help="serve: jobs in the Poisson stream")
     ap.add_argument("--load", type=float, default=0.8, help="serve: offered load (fraction of the plain method's "
                                                              "throughput)")
@@ -81,7 +87,7 @@ def rank_world():
 def workload_for(name, rank):
     if name == "batch32":  # the reference arm samples the first code of the batch
         return dict(code=synth.batch_codes([100 + 32 * rank])[0], **BATCH)
-    if name == "serve":  # the reference arm samples the largest code of the stream
+    if name in ("serve", "isfer"):  # the reference arm samples the largest code of the stream
         return dict(code=synth.serving_codes(2026, 8)[4], **SERVE_ENUM)
     w = dict(synth.workload(name))
     if rank:
@@ -267,12 +273,7 @@ def run_ours(args):
     clocks = clk.summary()
     total_ms = sum(times)
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        e = torch.tensor([eu, dec], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e)
-        eu_all, dec_all = float(e[0].item()), float(e[1].item())
+        total_ms, (eu_all, dec_all) = reduce_time_and_work(total_ms, [eu, dec], device="cuda")
     else:
         eu_all, dec_all = float(eu), float(dec)
     value = eu_all / (total_ms / 1e3)
@@ -364,7 +365,9 @@ def run_batch(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     tsx_build.build()
     # rank r takes seeds 100 + 32 r .. 131 + 32 r: independent batches of the same shape
-    codes = synth.batch_codes(range(100 + 32 * rank, 132 + 32 * rank))
+    seeds = ([int(x) for x in args.batch_seeds.split(",")] if args.batch_seeds
+             else list(range(100 + 32 * rank, 132 + 32 * rank)))
+    codes = synth.batch_codes(seeds)
     stream = torch.cuda.Stream()
     handles = [tsx.load_code(c, stream=stream) for c in codes]
     params = dict(BATCH, decoder=args.decoder)
@@ -406,12 +409,7 @@ def run_batch(args):
     total_ms = sum(times)
     eu, dec, nts = float(s["edge_updates"]) * args.steps, float(s["decodes"]) * args.steps, s["n_ts"]
     if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        e = torch.tensor([eu, dec], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e)
-        eu, dec = float(e[0].item()), float(e[1].item())
+        total_ms, (eu, dec) = reduce_time_and_work(total_ms, [eu, dec], device="cuda")
     value = eu / (total_ms / 1e3)
 
     # the same codes one enumerate_ts() at a time (eager, per-code launches)
@@ -470,7 +468,8 @@ def run_batch(args):
         "vs_baseline": None,
         "dtype": "int8" if args.decoder == "nms8" else "int16",
         "data": "synthetic",
-        "config": {"workload": "batch32", "codes": len(codes), "n_cand": int(s["n_cand"]),
+        "config": {"workload": "batch32" + (f"[{args.batch_seeds}]" if args.batch_seeds else ""),
+                   "codes": len(codes), "n_cand": int(s["n_cand"]),
                    "n_range": [min(c.n for c in codes), max(c.n for c in codes)], "decoder": args.decoder,
                    **BATCH, "tuned": bool(args.tune), "tiles": sorted({p.warps_per_cta for p in plist}),
                    "multi_code_launch": batch.multi_launch, "cuda_graph": True,
@@ -618,8 +617,103 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def isfer_setup(tsx, stream=None):
+    """The importance-sampling workload: the largest serving code (n = 8,832,
+    4 x 23 base, Z = 384), biased toward the lowest-threshold trapping set
+    among its first 2,000 candidates, at Eb/N0 = 4 dB, mu = 1."""
+    code = synth.serving_codes(2026, 8)[4]
+    h = tsx.load_code(code, stream=stream)
+    v = tsx.ts_list_view(tsx.enumerate_ts(h, stream=stream, **dict(SERVE_ENUM, cand_end=2000)))
+    thr = np.where(v["thr"] >= 0, v["thr"], 1 << 30)
+    return code, h, v["keys"][int(np.argmin(thr))]
+
+
+def run_isfer(args):
+    import torch
+    import paper_2208_05795_gb300 as tsx
+    from paper_2208_05795_gb300 import build as tsx_build
+
+    rank, world, local = rank_world()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    tsx_build.build()
+    stream = torch.cuda.Stream()
+    code, h, ts = isfer_setup(tsx, stream)
+    kw = dict(ebn0_db=4.0, mu=1.0, n_samples=args.samples)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for i in range(args.warmup):
+        tsx.is_fer_estimate(h, ts, stream=stream, job_key=10_000 + i, **kw)
+    if dist:
+        dist.barrier()
+    ms, eu, nf, fer = [], 0, 0, []
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            # the step's own job key: rank r, step i (independent sample streams)
+            r = tsx.is_fer_estimate(h, ts, stream=stream, job_key=(rank << 32) | i, **kw)
+            ms.append(r["ms"])
+            eu += r["edge_updates"]
+            nf += r["n_fail"]
+            fer.append(r["fer"])
+    clocks = clk.summary()
+    total_ms = sum(ms)
+    samples = float(args.samples) * args.steps
+    if dist:
+        total_ms, (samples, eu) = reduce_time_and_work(total_ms, [samples, eu], device="cuda")
+    # end to end: the public call from host arrays (the set's nodes) to the host result
+    t0 = time.perf_counter()
+    tsx.is_fer_estimate(h, ts, stream=stream, job_key=99, **kw)
+    e2e_s = time.perf_counter() - t0
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peak = INT_LANES_PER_SM * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = ALG_OPS_PER_EDGE * (eu / args.steps if not dist else eu / world / args.steps) / (
+        sum(ms) / len(ms) / 1e3) / 1e12
+    line = {
+        "metric": "importance-sampling samples/s",
+        "value": samples / (total_ms / 1e3),
+        "unit": "samples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int16",
+        "data": "synthetic",
+        "config": {"workload": "isfer", "code": code.name, "n": code.n, "m": code.m, "a": len(ts),
+                   "ebn0_db": 4.0, "mu": 1.0, "samples_per_step": args.samples, "K": 20,
+                   "parallelism": f"replicas{world}", "l2": "flushed before each step (256 MB write)"},
+        "edge_updates_per_s": eu / (total_ms / 1e3),
+        "fer_mean": float(np.mean(fer)), "fails_per_step": nf / args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+                     "traffic": None, "note": "12 int ops per edge update of the decodes; the noise generation "
+                                              "is extra work not counted"},
+        "cpu_baseline": None,
+        "e2e": {"value": args.samples / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 4 * len(ts),
+                "d2h_bytes_per_step": 96},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.workload == "isfer" and args.impl != "reference":
+        run_isfer(args)
+        return
     if args.workload == "serve" and args.impl != "reference":
         run_serve(args)
         return

@@ -67,7 +67,7 @@ SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
 constexpr int kSmemCta = 226 * 1024;
 
 bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_per_sm, int num_sms,
-          LaunchShape *out) {
+          LaunchShape *out, int max_warps = 16) {
     LaunchShape sh{};
     sh.lay = make_layout(g, decoder, kind);
     const int room = kSmemCta - sh.lay.tables_bytes;
@@ -85,7 +85,7 @@ bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_p
         if (G > 16) G = 16;
         if (G < 1) G = 1;
     }
-    int gmax_cta = 16 / G;  // at most 512 threads per CTA
+    int gmax_cta = max_warps / G;  // at most 32 * max_warps threads per CTA
     if (gmax_cta < 1) gmax_cta = 1;
     if (gmax_cta > fit) gmax_cta = fit;
     if (G > 1 && gmax_cta > 15) gmax_cta = 15;  // named barriers 1..15
@@ -120,7 +120,7 @@ cudaError_t launch_decode(const DevCode &g, const DecodeParams &dp, const EnumBu
     LaunchShape sh;
     // the two-codeword kernel where its bounds hold and its layout fits a CTA
     const bool pair = !force_scalar && pair_ok(g, dp) && plan(g, dp.decoder, kLayPair, G, groups, ctas_per_sm,
-                                                             num_sms, &sh);
+                                                             num_sms, &sh, kPairWarps);
     if (!pair && !plan(g, dp.decoder, kLayScalar, G, groups, ctas_per_sm, num_sms, &sh))
         return cudaErrorInvalidConfiguration;
     switch (dp.decoder) {

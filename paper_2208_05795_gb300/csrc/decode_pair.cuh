@@ -219,6 +219,72 @@ struct PairDecoder {
         return (int)(((unsat >> 15) & 1u) | ((unsat >> 30) & 2u));
     }
 
+    // Two checks of one QC row block at once (rows r and r + dr, 16-bit
+    // storage, large degree): the same steps as check_node_twopass for both,
+    // interleaved edge by edge, so that the two dependency chains overlap and
+    // each position's shift is read once for both rows.  Returns the
+    // unsatisfied flags of row r in bits 0/1 and of row r + dr in bits 2/3.
+    __device__ __forceinline__ int check_rows2(int deg, unsigned km, unsigned kb, bool writeR,
+                                               const unsigned char *Pc, unsigned char *Pn, const int32_t *rjz,
+                                               const int16_t *rs, int rb, int r, int dr) const {
+        const int Z = g.Z;
+        unsigned spA = 0, sxA = 0, m1A = pc.BS2, m2A = pc.BS2;
+        unsigned spB = 0, sxB = 0, m1B = pc.BS2, m2B = pc.BS2;
+        const int r2 = r + dr;
+#pragma unroll 2
+        for (int p = 0; p < deg; p++) {
+            const int jz = rjz[p], sh = rs[p];
+            const int tA = r + sh, tB = r2 + sh;
+            const int poA = 4 * (jz + (int)min((unsigned)tA, (unsigned)(tA - Z)));
+            const int poB = 4 * (jz + (int)min((unsigned)tB, (unsigned)(tB - Z)));
+            const int roA = rb + (p * Z + r) * RSZ, roB = roA + dr * RSZ;
+            const unsigned xA = *(const unsigned *)(Pc + poA), xB = *(const unsigned *)(Pc + poB);
+            const unsigned yA = (ldR(roA) & km) | kb, yB = (ldR(roB) & km) | kb;
+            spA ^= xA;
+            spB ^= xB;
+            unsigned qA, aA, qB, aB;
+            edge_q(xA, yA, qA, aA);
+            edge_q(xB, yB, qB, aB);
+            if (writeR) {
+                stR(roA, qA);
+                stR(roB, qB);
+            }
+            sxA ^= qA;
+            sxB ^= qB;
+            m2A = vminu2(m2A, vmaxu2(m1A, aA));
+            m1A = vminu2(m1A, aA);
+            m2B = vminu2(m2B, vmaxu2(m1B, aB));
+            m1B = vminu2(m1B, aB);
+        }
+        const unsigned dodd = (deg & 1) ? 0x80008000u : 0u;
+        const unsigned unsatA = (spA ^ dodd) & 0x80008000u, unsatB = (spB ^ dodd) & 0x80008000u;
+        if (writeR) {
+            const unsigned o1A = (((m1A - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o2A = (((m2A - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o1B = (((m1B - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o2B = (((m2B - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned odd = ((deg - 1) & 1) ? 0x80008000u : 0u;
+            const unsigned sxkA = sxA ^ odd, sxkB = sxB ^ odd;
+#pragma unroll 2
+            for (int p = 0; p < deg; p++) {
+                const int jz = rjz[p], sh = rs[p];
+                const int tA = r + sh, tB = r2 + sh;
+                const int poA = 4 * (jz + (int)min((unsigned)tA, (unsigned)(tA - Z)));
+                const int poB = 4 * (jz + (int)min((unsigned)tB, (unsigned)(tB - Z)));
+                const int roA = rb + (p * Z + r) * RSZ, roB = roA + dr * RSZ;
+                const unsigned qA = ldR(roA), qB = ldR(roB);
+                const unsigned aA = vmaxu2(qA, (~qA) + 0x00010001u), aB = vmaxu2(qB, (~qB) + 0x00010001u);
+                const unsigned rnA = edge_out(qA, aA, m1A, o1A, o2A, sxkA);
+                const unsigned rnB = edge_out(qB, aB, m1B, o1B, o2B, sxkB);
+                stR(roA, rnA);
+                stR(roB, rnB);
+                red_add(Pn + poA, rnA);
+                red_add(Pn + poB, rnB);
+            }
+        }
+        return (int)(((unsatA >> 15) & 1u) | ((unsatA >> 30) & 2u) | ((unsatB >> 13) & 4u) | ((unsatB >> 28) & 8u));
+    }
+
     // check pass; returns u of half 0 in the low 16 bits and half 1 above
     __device__ __forceinline__ int check_pass(unsigned km, unsigned kb, bool writeR, const unsigned *Pcur,
                                               unsigned *Pnext) const {
@@ -254,7 +320,16 @@ struct PairDecoder {
                 } else {
                     const int32_t *rjz = sg.rjz + i * g.dc_max;
                     const int16_t *rs = sg.rs + i * g.dc_max;
-                    for (int r = gp.gt; r < Z; r += gp.T) {
+                    int r = gp.gt;
+                    if constexpr (!I8) {
+                        // rows in pairs (r, r + T) while both exist
+                        for (; r + gp.T < Z; r += 2 * gp.T) {
+                            const int f = check_rows2(deg, km, kb, writeR, Pc, Pn, rjz, rs, rb, r, gp.T);
+                            u0 += (f & 1) + ((f >> 2) & 1);
+                            u1 += ((f >> 1) & 1) + (f >> 3);
+                        }
+                    }
+                    for (; r < Z; r += gp.T) {
                         const int f = check_node(
                             deg, km, kb, writeR, Pc, Pn,
                             [&](int p) {
@@ -547,7 +622,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
 }
 
 template <bool QC, int DC, bool EXACT, bool I8>
-__global__ void __launch_bounds__(512) pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay,
+__global__ void __launch_bounds__(32 * kPairWarps) pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay,
                                                    int G) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SGraph sg = load_tables(g, smem);

@@ -66,6 +66,11 @@ struct BatchItem {
 // All items of a multi-code launch, passed by value as one kernel parameter
 // (kernel parameters may take up to 32 KB).
 constexpr int kMaxBatch = 64;
+
+// warps per CTA of the single-code two-codeword kernel (its launch bound):
+// 20 warps keep the (3,6)-regular general-code variant at 96 registers
+// without spills and measured faster than 16 or 24
+constexpr int kPairWarps = 20;
 struct BatchArgs {
     BatchItem it[kMaxBatch];
 };
