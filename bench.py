@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--workload", default="peg1008",
                     choices=sorted(synth.WORKLOADS) + ["batch32", "serve", "isfer"])
     ap.add_argument("--samples", type=int, default=1_000_000, help="isfer: samples per step")
+    ap.add_argument("--no-graph", action="store_true", help="batch32: launch each step eagerly instead of "
+                                                             "replaying the captured graph")
     ap.add_argument("--batch-seeds", default="", help="batch32: comma-separated code seeds instead of 100..131 "
                                                       "(a bounded case for profiling)")
     ap.add_argument("--jobs", type=int, default=120, help="serve: jobs in the Poisson stream")
@@ -383,11 +385,16 @@ def run_batch(args):
     for _ in range(2):
         tsx.batch_run(batch, stream=stream)
     stream.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph, stream=stream):
-        tsx.batch_run(batch, stream=stream)
+    if args.no_graph:  # eager launches (for a profiler that does not follow stream capture)
+        def replay():
+            tsx.batch_run(batch, stream=stream)
+    else:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            tsx.batch_run(batch, stream=stream)
+        replay = graph.replay
     for _ in range(args.warmup):
-        graph.replay()
+        replay()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -399,7 +406,7 @@ def run_batch(args):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                graph.replay()
+                replay()
                 e1.record(stream)
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -472,7 +479,7 @@ def run_batch(args):
                    "codes": len(codes), "n_cand": int(s["n_cand"]),
                    "n_range": [min(c.n for c in codes), max(c.n for c in codes)], "decoder": args.decoder,
                    **BATCH, "tuned": bool(args.tune), "tiles": sorted({p.warps_per_cta for p in plist}),
-                   "multi_code_launch": batch.multi_launch, "cuda_graph": True,
+                   "multi_code_launch": batch.multi_launch, "cuda_graph": not args.no_graph,
                    "parallelism": f"replicas{world}", "l2": "flushed before each step (256 MB write)"},
         "decodes_per_s": dec / (total_ms / 1e3),
         "n_ts": int(nts),
