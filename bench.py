@@ -310,6 +310,14 @@ def run_ours(args):
         return
     peak = INT_LANES_PER_SM * N_SMS * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s
     avg_dec_ms = sum(ms_dec) / len(ms_dec)
+    # DRAM bytes (read + write) of one decode launch: an ncu capture of this kernel on the PEG
+    # workload's first 40,000 candidates read 734,464 B and wrote none (candidate sets in, records
+    # out, both proportional to the candidates), scaled to the launch's candidates
+    traffic, traffic_note = None, "not captured for this workload"
+    if args.workload == "peg1008" and args.decoder == "nms16":
+        traffic = 734464.0 / 40000 * float(s["n_cand"])
+        traffic_note = "scaled by candidates from an ncu capture of the first 40,000 (734,464 B)"
+
     eu_per_step = eu / args.steps
     achieved = ALG_OPS_PER_EDGE * eu_per_step / (avg_dec_ms / 1e3) / 1e12
     cpu = cpu_baseline(w, args.decoder, args.cpu_seconds)[0] if args.cpu_seconds > 0 else None
@@ -337,7 +345,7 @@ def run_ours(args):
         "ms_decode_kernel": avg_dec_ms,
         "ms_candidates": sum(ms_cand) / len(ms_cand),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                      "note": f"{ALG_OPS_PER_EDGE} int ops per edge update; peak = {INT_LANES_PER_SM} lanes x "
                              f"{N_SMS} SMs x {SM_MAX_MHZ:.0f} MHz"},
         "cpu_baseline": cpu,
