@@ -75,8 +75,8 @@ bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_p
     if (fit < 1) return false;
     if (kind == kLaySieve) G = 1;
     if (G <= 0) {
-        const int want_warps = 24;
-        G = (want_warps + fit - 1) / fit;
+        // as many codeword groups as fit (up to one per warp), the warps shared among them
+        G = max_warps / (fit < max_warps ? fit : max_warps);
         int work = g.m < g.n ? g.m : g.n;
         if (g.kind == TSX_CODE_QC && g.Z < work) work = g.Z;  // QC passes run block by block
         int gmax = work / 32;
