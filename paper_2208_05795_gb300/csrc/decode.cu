@@ -27,7 +27,7 @@ int post_bytes(int decoder) { return decoder == TSX_DEC_SPA_F32 ? 4 : 2; }
 
 SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
     SlotLayout L{};
-    L.tables_bytes = al16(tab_offsets(g).total);
+    L.tables_bytes = al16(tab_offsets(g, kind == kLayPair || kind == kLayIs).total);
     const int nw = (g.n + 31) / 32;
     // message slots: QC edges, or the position-major m x dc_max grid of a CSR code
     const int nmsg = g.kind == TSX_CODE_QC ? g.E : g.m * g.dc_max;

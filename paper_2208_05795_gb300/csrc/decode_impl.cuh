@@ -54,7 +54,9 @@ struct TabOff {
     int total;
 };
 
-__host__ __device__ inline TabOff tab_offsets(const DevCode &g) {
+// pair = the tables of the two-codeword kernels, which have no variable-node
+// pass and so no per-variable edge lists (general codes)
+__host__ __device__ inline TabOff tab_offsets(const DevCode &g, bool pair = false) {
     TabOff o{};
     int x = 0;
     if (g.kind == TSX_CODE_QC) {
@@ -70,7 +72,7 @@ __host__ __device__ inline TabOff tab_offsets(const DevCode &g) {
         o.c_ptr = x; x += al16((g.m + 1) * 2);
         o.c_vn = x; x += al16(g.E * 2);
         o.v_ptr = x; x += al16((g.n + 1) * 2);
-        o.v_edge = x; x += al16(g.E * 2);
+        if (!pair) { o.v_edge = x; x += al16(g.E * 2); }
     }
     o.total = x;
     return o;
@@ -101,8 +103,8 @@ __device__ void copy_bytes(void *dst, const void *src, int bytes) {
     }
 }
 
-__device__ SGraph load_tables(const DevCode &g, unsigned char *sm) {
-    TabOff o = tab_offsets(g);
+__device__ SGraph load_tables(const DevCode &g, unsigned char *sm, bool pair = false) {
+    TabOff o = tab_offsets(g, pair);
     SGraph s{};
     if (g.kind == TSX_CODE_QC) {
         copy_bytes(sm + o.rdeg, g.rdeg, g.m_b * 2);
@@ -125,11 +127,13 @@ __device__ SGraph load_tables(const DevCode &g, unsigned char *sm) {
         copy_bytes(sm + o.c_ptr, g.c_ptr, (g.m + 1) * 2);
         copy_bytes(sm + o.c_vn, g.c_vn, g.E * 2);
         copy_bytes(sm + o.v_ptr, g.v_ptr, (g.n + 1) * 2);
-        copy_bytes(sm + o.v_edge, g.v_edge, g.E * 2);
         s.c_ptr = (const uint16_t *)(sm + o.c_ptr);
         s.c_vn = (const uint16_t *)(sm + o.c_vn);
         s.v_ptr = (const uint16_t *)(sm + o.v_ptr);
-        s.v_edge = (const uint16_t *)(sm + o.v_edge);
+        if (!pair) {
+            copy_bytes(sm + o.v_edge, g.v_edge, g.E * 2);
+            s.v_edge = (const uint16_t *)(sm + o.v_edge);
+        }
     }
     return s;
 }

@@ -625,7 +625,7 @@ template <bool QC, int DC, bool EXACT, bool I8>
 __global__ void __launch_bounds__(32 * kPairWarps) pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay,
                                                    int G) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SGraph sg = load_tables(g, smem);
+    const SGraph sg = load_tables(g, smem, true);
     __syncthreads();
     pair_run<QC, DC, EXACT, I8>(g, dp, b, lay, G, sg, smem, (threadIdx.x >> 5) / G);
 }
@@ -642,7 +642,7 @@ __global__ void __launch_bounds__(512) batch_kernel(const __grid_constant__ Batc
     extern __shared__ __align__(16) unsigned char smem[];
     for (int c = 0; c < n_items; c++) {
         const BatchItem &it = args.it[c];
-        const SGraph sg = load_tables(it.g, smem);
+        const SGraph sg = load_tables(it.g, smem, true);
         __syncthreads();
         const int grp = (threadIdx.x >> 5) / it.G;
         if (grp < it.groups) pair_run<QC, DC, EXACT, I8>(it.g, it.dp, it.b, it.lay, it.G, sg, smem, grp);

@@ -141,7 +141,7 @@ struct IsArgs {
 template <bool QC, int DC, bool EXACT>
 __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsArgs ia, SlotLayout lay, int G) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const SGraph sg = load_tables(g, smem);
+    const SGraph sg = load_tables(g, smem, true);
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = warp / G;
