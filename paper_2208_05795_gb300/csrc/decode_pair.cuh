@@ -57,7 +57,7 @@ __device__ __forceinline__ void red_add(unsigned char *addr, unsigned v) {
 constexpr unsigned kBeta = 0x8000u;
 
 struct PairConst {
-    unsigned B2, BS2, LO2, HI2, BETA2, amask2;
+    unsigned B2, BS2, LO2, HI2, BETA2, amask2;  // LO2 / HI2: clamp bounds of q'' = q + beta
     int B, sat, an, as;
 };
 
@@ -97,35 +97,51 @@ struct PairDecoder {
         else *(unsigned *)(Rb + byteoff) = v;
     }
 
+    // an edge's incoming message; MASK: some half starts a decode in this
+    // pass and reads the zero message B there (km keeps the other half, kb
+    // supplies B)
+    template <bool MASK>
+    __device__ __forceinline__ unsigned ldy(int byteoff, unsigned km, unsigned kb) const {
+        if constexpr (MASK) return (ldR(byteoff) & km) | kb;
+        else return ldR(byteoff);
+    }
+
     // One check node.  pv(p): byte offset of P'[v_p]; re(p): byte offset of
     // R'[e_p].  Reads Pc, adds the new messages into Pn.  Returns the
     // unsatisfied flags of both halves in bits 0/1.
-    template <class PV, class RE>
+    template <bool MASK, class PV, class RE>
     __device__ __forceinline__ int check_node(int deg, unsigned km, unsigned kb, bool writeR, const unsigned char *Pc,
                                               unsigned char *Pn, PV pv, RE re) const {
-        if constexpr (DC <= 8) return check_node_regs(deg, km, kb, writeR, Pc, Pn, pv, re);
-        else return check_node_twopass(deg, km, kb, writeR, Pc, Pn, pv, re);
+        if constexpr (DC <= 8) return check_node_regs<MASK>(deg, km, kb, writeR, Pc, Pn, pv, re);
+        else return check_node_twopass<MASK>(deg, km, kb, writeR, Pc, Pn, pv, re);
     }
 
     // extrinsic value q'' = clamp(q) + beta and magnitude |q| + beta of one edge
     __device__ __forceinline__ void edge_q(unsigned x, unsigned y, unsigned &q, unsigned &a) const {
-        q = vminu2(vmaxu2(x - y, pc.LO2), pc.HI2) + pc.B2;
+        q = vminu2(vmaxu2(x - y + pc.B2, pc.LO2), pc.HI2);
         a = vmaxu2(q, (~q) + 0x00010001u);
     }
 
     // the new message of an edge from its q'', |q|, the check's min1, the
     // two output magnitudes and the sign parity of all its edges
-    __device__ __forceinline__ unsigned edge_out(unsigned q, unsigned a, unsigned m1, unsigned o1, unsigned o2,
+    // (the four possible outputs B +- o1, B +- o2 are formed once per check)
+    struct Outs {
+        unsigned p1, n1, p2, n2;
+    };
+    __device__ __forceinline__ Outs outs(unsigned o1, unsigned o2) const {
+        return Outs{pc.B2 + o1, pc.B2 - o1, pc.B2 + o2, pc.B2 - o2};
+    }
+    __device__ __forceinline__ unsigned edge_out(unsigned q, unsigned a, unsigned m1, const Outs &o,
                                                  unsigned sxk) const {
         const unsigned neg = spread15(sxk ^ q);                  // 0xFFFF: others' sign product < 0
         const unsigned ne = spread15(a - m1 + 0x7FFF7FFFu);      // 0xFFFF: |q_p| != min1
-        const unsigned mag = (o1 & ne) | (o2 & ~ne);
-        const unsigned pos = pc.B2 + mag, ng = pc.B2 - mag;
-        return (ng & neg) | (pos & ~neg);
+        const unsigned t1 = (o.n1 & neg) | (o.p1 & ~neg);        // +-o1
+        const unsigned t2 = (o.n2 & neg) | (o.p2 & ~neg);        // +-o2
+        return (t1 & ne) | (t2 & ~ne);
     }
 
     // small degree: the edges' q and |q| stay in registers between the passes
-    template <class PV, class RE>
+    template <bool MASK, class PV, class RE>
     __device__ __forceinline__ int check_node_regs(int deg, unsigned km, unsigned kb, bool writeR,
                                                    const unsigned char *Pc, unsigned char *Pn, PV pv, RE re) const {
         unsigned sp = 0, sx = 0, m1 = pc.BS2, m2 = pc.BS2;
@@ -136,7 +152,7 @@ struct PairDecoder {
             if (EXACT || p < deg) {
                 po[p] = pv(p);
                 const unsigned x = *(const unsigned *)(Pc + po[p]);
-                const unsigned y = (ldR(re(p)) & km) | kb;
+                const unsigned y = ldy<MASK>(re(p), km, kb);
                 sp ^= x;
                 unsigned q, a;
                 edge_q(x, y, q, a);
@@ -155,13 +171,14 @@ struct PairDecoder {
             const unsigned d1 = m1 - pc.BETA2, d2 = m2 - pc.BETA2;
             const unsigned o1 = ((d1 * (unsigned)pc.an) >> pc.as) & pc.amask2;
             const unsigned o2 = ((d2 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const Outs oo = outs(o1, o2);
             // bit 15 of sx ^ q_p = parity of #(q >= 0) over the other edges;
             // negatives among the others = (deg - 1) - that
             const unsigned sxk = sx ^ (((deg - 1) & 1) ? 0x80008000u : 0u);
 #pragma unroll
             for (int p = 0; p < DC; p++) {
                 if (EXACT || p < deg) {
-                    const unsigned rn = edge_out(qs[p], as_[p], m1, o1, o2, sxk);
+                    const unsigned rn = edge_out(qs[p], as_[p], m1, oo, sxk);
                     stR(re(p), rn);
                     red_add(Pn + po[p], rn);
                 }
@@ -173,7 +190,7 @@ struct PairDecoder {
     // large degree: the first pass leaves each edge's q'' in its message slot
     // (16-bit storage: a slot holds both halves' q''), the second reads it
     // back; with 8-bit storage the second pass reloads P and recomputes q
-    template <class PV, class RE>
+    template <bool MASK, class PV, class RE>
     __device__ __forceinline__ int check_node_twopass(int deg, unsigned km, unsigned kb, bool writeR,
                                                       const unsigned char *Pc, unsigned char *Pn, PV pv,
                                                       RE re) const {
@@ -182,7 +199,7 @@ struct PairDecoder {
         for (int p = 0; p < deg; p++) {
             const int ro = re(p);
             const unsigned x = *(const unsigned *)(Pc + pv(p));
-            const unsigned y = (ldR(ro) & km) | kb;
+            const unsigned y = ldy<MASK>(ro, km, kb);
             sp ^= x;
             unsigned q, a;
             edge_q(x, y, q, a);
@@ -198,6 +215,7 @@ struct PairDecoder {
             const unsigned d1 = m1 - pc.BETA2, d2 = m2 - pc.BETA2;
             const unsigned o1 = ((d1 * (unsigned)pc.an) >> pc.as) & pc.amask2;
             const unsigned o2 = ((d2 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const Outs oo = outs(o1, o2);
             const unsigned sxk = sx ^ (((deg - 1) & 1) ? 0x80008000u : 0u);
 #pragma unroll 4
             for (int p = 0; p < deg; p++) {
@@ -208,10 +226,10 @@ struct PairDecoder {
                     a = vmaxu2(q, (~q) + 0x00010001u);
                 } else {
                     const unsigned x = *(const unsigned *)(Pc + po);
-                    const unsigned y = (ldR(ro) & km) | kb;
+                    const unsigned y = ldy<MASK>(ro, km, kb);
                     edge_q(x, y, q, a);
                 }
-                const unsigned rn = edge_out(q, a, m1, o1, o2, sxk);
+                const unsigned rn = edge_out(q, a, m1, oo, sxk);
                 stR(ro, rn);
                 red_add(Pn + po, rn);
             }
@@ -224,6 +242,7 @@ struct PairDecoder {
     // interleaved edge by edge, so that the two dependency chains overlap and
     // each position's shift is read once for both rows.  Returns the
     // unsatisfied flags of row r in bits 0/1 and of row r + dr in bits 2/3.
+    template <bool MASK>
     __device__ __forceinline__ int check_rows2(int deg, unsigned km, unsigned kb, bool writeR,
                                                const unsigned char *Pc, unsigned char *Pn, const int32_t *rjz,
                                                const int16_t *rs, int rb, int r, int dr) const {
@@ -239,7 +258,7 @@ struct PairDecoder {
             const int poB = 4 * (jz + (int)min((unsigned)tB, (unsigned)(tB - Z)));
             const int roA = rb + (p * Z + r) * RSZ, roB = roA + dr * RSZ;
             const unsigned xA = *(const unsigned *)(Pc + poA), xB = *(const unsigned *)(Pc + poB);
-            const unsigned yA = (ldR(roA) & km) | kb, yB = (ldR(roB) & km) | kb;
+            const unsigned yA = ldy<MASK>(roA, km, kb), yB = ldy<MASK>(roB, km, kb);
             spA ^= xA;
             spB ^= xB;
             unsigned qA, aA, qB, aB;
@@ -263,6 +282,7 @@ struct PairDecoder {
             const unsigned o2A = (((m2A - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
             const unsigned o1B = (((m1B - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
             const unsigned o2B = (((m2B - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const Outs ooA = outs(o1A, o2A), ooB = outs(o1B, o2B);
             const unsigned odd = ((deg - 1) & 1) ? 0x80008000u : 0u;
             const unsigned sxkA = sxA ^ odd, sxkB = sxB ^ odd;
 #pragma unroll 2
@@ -274,8 +294,8 @@ struct PairDecoder {
                 const int roA = rb + (p * Z + r) * RSZ, roB = roA + dr * RSZ;
                 const unsigned qA = ldR(roA), qB = ldR(roB);
                 const unsigned aA = vmaxu2(qA, (~qA) + 0x00010001u), aB = vmaxu2(qB, (~qB) + 0x00010001u);
-                const unsigned rnA = edge_out(qA, aA, m1A, o1A, o2A, sxkA);
-                const unsigned rnB = edge_out(qB, aB, m1B, o1B, o2B, sxkB);
+                const unsigned rnA = edge_out(qA, aA, m1A, ooA, sxkA);
+                const unsigned rnB = edge_out(qB, aB, m1B, ooB, sxkB);
                 stR(roA, rnA);
                 stR(roB, rnB);
                 red_add(Pn + poA, rnA);
@@ -286,6 +306,7 @@ struct PairDecoder {
     }
 
     // check pass; returns u of half 0 in the low 16 bits and half 1 above
+    template <bool MASK>
     __device__ __forceinline__ int check_pass(unsigned km, unsigned kb, bool writeR, const unsigned *Pcur,
                                               unsigned *Pnext) const {
         int u0 = 0, u1 = 0;
@@ -307,7 +328,7 @@ struct PairDecoder {
                         }
                     }
                     for (int r = gp.gt; r < Z; r += gp.T) {
-                        const int f = check_node(
+                        const int f = check_node<MASK>(
                             deg, km, kb, writeR, Pc, Pn,
                             [&](int p) {
                                 const int t = r + rsh[p];
@@ -324,13 +345,13 @@ struct PairDecoder {
                     if constexpr (!I8) {
                         // rows in pairs (r, r + T) while both exist
                         for (; r + gp.T < Z; r += 2 * gp.T) {
-                            const int f = check_rows2(deg, km, kb, writeR, Pc, Pn, rjz, rs, rb, r, gp.T);
+                            const int f = check_rows2<MASK>(deg, km, kb, writeR, Pc, Pn, rjz, rs, rb, r, gp.T);
                             u0 += (f & 1) + ((f >> 2) & 1);
                             u1 += ((f >> 1) & 1) + (f >> 3);
                         }
                     }
                     for (; r < Z; r += gp.T) {
-                        const int f = check_node(
+                        const int f = check_node<MASK>(
                             deg, km, kb, writeR, Pc, Pn,
                             [&](int p) {
                                 const int t = r + rs[p];
@@ -347,7 +368,7 @@ struct PairDecoder {
             for (int c = gp.gt; c < m; c += gp.T) {
                 const int e0 = sg.c_ptr[c];
                 const int deg = EXACT ? DC : sg.c_ptr[c + 1] - e0;
-                const int f = check_node(
+                const int f = check_node<MASK>(
                     deg, km, kb, writeR, Pc, Pn, [&](int p) { return 4 * (int)sg.c_vn[e0 + p]; },
                     [&](int p) { return (p * m + c) * RSZ; });
                 u0 += f & 1;
@@ -435,8 +456,8 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     pc.B2 = (unsigned)pc.B * 0x00010001u;
     pc.BETA2 = kBeta * 0x00010001u;
     pc.BS2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
-    pc.LO2 = (kBeta - (unsigned)pc.B - (unsigned)pc.sat) * 0x00010001u;
-    pc.HI2 = (kBeta - (unsigned)pc.B + (unsigned)pc.sat) * 0x00010001u;
+    pc.LO2 = (kBeta - (unsigned)pc.sat) * 0x00010001u;
+    pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     PairDecoder<QC, DC, EXACT, I8> dec{g, sg, gp, pc, Rb};
 
@@ -550,7 +571,8 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         const unsigned kb = pc.B2 & ~km;
         const bool wr = (H[0].idx >= 0 && H[0].k < dp.K) || (H[1].idx >= 0 && H[1].k < dp.K);
         // u_k of both halves from P_k = Pc; Pn accumulates P_{k+1}
-        const int us = dec.check_pass(km, kb, wr, Pc, Pn);
+        const int us = km != 0xFFFFFFFFu ? dec.template check_pass<true>(km, kb, wr, Pc, Pn)
+                                         : dec.template check_pass<false>(km, kb, wr, Pc, Pn);
         int restart[2] = {0, 0};
         for (int hh = 0; hh < 2; hh++) {
             Half &h = H[hh];

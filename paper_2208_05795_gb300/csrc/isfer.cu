@@ -169,8 +169,8 @@ __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsA
     pc.B2 = (unsigned)pc.B * 0x00010001u;
     pc.BETA2 = kBeta * 0x00010001u;
     pc.BS2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
-    pc.LO2 = (kBeta - (unsigned)pc.B - (unsigned)pc.sat) * 0x00010001u;
-    pc.HI2 = (kBeta - (unsigned)pc.B + (unsigned)pc.sat) * 0x00010001u;
+    pc.LO2 = (kBeta - (unsigned)pc.sat) * 0x00010001u;
+    pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     PairDecoder<QC, DC, EXACT, false> dec{g, sg, gp, pc, Rb};
 
@@ -233,7 +233,8 @@ __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsA
         const unsigned km = (first[0] ? 0xFFFF0000u : 0xFFFFFFFFu) & (first[1] ? 0x0000FFFFu : 0xFFFFFFFFu);
         const unsigned kb = pc.B2 & ~km;
         const bool wr = (sidx[0] >= 0 && k[0] < dp.K) || (sidx[1] >= 0 && k[1] < dp.K);
-        const int us = dec.check_pass(km, kb, wr, Pc, Pn);
+        const int us = km != 0xFFFFFFFFu ? dec.template check_pass<true>(km, kb, wr, Pc, Pn)
+                                         : dec.template check_pass<false>(km, kb, wr, Pc, Pn);
         int restart[2] = {0, 0};
         for (int hh = 0; hh < 2; hh++) {
             if (sidx[hh] < 0) continue;
