@@ -298,6 +298,11 @@ extern "C" int load_code(const tsx_code_desc *desc, void *stream, tsx_code **out
     DevCode &d = c->d;
     d.kind = h.kind; d.n = h.n; d.m = h.m; d.E = h.E; d.Z = h.Z; d.n_b = h.n_b; d.m_b = h.m_b;
     d.dv_max = h.dv_max; d.dc_max = h.dc_max; d.girth = girth;
+    d.dv_min = h.dv_max;
+    if (h.kind == TSX_CODE_QC)
+        for (int j = 0; j < h.n_b; j++) d.dv_min = std::min<int>(d.dv_min, h.cdeg[j]);
+    else
+        for (int v = 0; v < h.n; v++) d.dv_min = std::min<int>(d.dv_min, h.v_ptr[v + 1] - h.v_ptr[v]);
     d.dc_min = h.dc_max;
     for (int c = 0; c < (h.kind == TSX_CODE_QC ? h.m_b : h.m); c++) {
         const int dc = h.kind == TSX_CODE_QC ? h.rdeg[c] : h.c_ptr[c + 1] - h.c_ptr[c];

@@ -385,6 +385,16 @@ struct PairDecoder {
 
     // the accumulator: L'(v) = L + beta - dv B in both halves (impulse
     // nodes are patched afterwards)
+    // a run of equal words, 16 bytes per store where the run is aligned
+    __device__ __forceinline__ void fill(unsigned *row, int count, unsigned w) const {
+        if (((uintptr_t)row & 15) == 0 && (count & 3) == 0) {
+            uint4 *r4 = (uint4 *)row;
+            const uint4 w4 = make_uint4(w, w, w, w);
+            for (int k = gp.gt; k < (count >> 2); k += gp.T) r4[k] = w4;
+        } else {
+            for (int k = gp.gt; k < count; k += gp.T) row[k] = w;
+        }
+    }
     __device__ __forceinline__ void init_accum(unsigned *Pn, int Lb) const {
         if constexpr (QC) {
             const int Z = g.Z;
@@ -394,6 +404,9 @@ struct PairDecoder {
                 unsigned *row = Pn + j * Z;
                 for (int k = gp.gt; k < Z; k += gp.T) row[k] = l2;
             }
+        } else if (g.dv_min == g.dv_max) {  // variable-regular: one value
+            const unsigned l = (unsigned)(Lb + (int)kBeta - g.dv_max * pc.B);
+            fill(Pn, g.n, l | (l << 16));
         } else {
             for (int v = gp.gt; v < g.n; v += gp.T) {
                 const unsigned l = (unsigned)(Lb + (int)kBeta - vdeg(v) * pc.B);

@@ -29,6 +29,7 @@ struct DevCode {
     int n, m, E, Z, n_b, m_b;
     int dv_max, dc_max;
     int dc_min;         // smallest check degree (dc_min == dc_max: check-regular)
+    int dv_min;         // smallest variable degree (dv_min == dv_max: variable-regular)
     int girth, wstart;  // wstart = max(1, girth/2)
     int n_rep;
     // QC tables
