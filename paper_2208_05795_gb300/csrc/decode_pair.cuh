@@ -58,6 +58,7 @@ constexpr unsigned kBeta = 0x8000u;
 
 struct PairConst {
     unsigned B2, BS2, LO2, HI2, BETA2, amask2;  // LO2 / HI2: clamp bounds of q'' = q + beta
+    unsigned BAN2;  // BETA2 * alpha_num: (m - beta) an = m an - BAN2 (mod 2^32)
     int B, sat, an, as;
 };
 
@@ -168,9 +169,8 @@ struct PairDecoder {
         const unsigned dodd = (deg & 1) ? 0x80008000u : 0u;
         const unsigned unsat = (sp ^ dodd) & 0x80008000u;
         if (writeR) {
-            const unsigned d1 = m1 - pc.BETA2, d2 = m2 - pc.BETA2;
-            const unsigned o1 = ((d1 * (unsigned)pc.an) >> pc.as) & pc.amask2;
-            const unsigned o2 = ((d2 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o1 = ((m1 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
+            const unsigned o2 = ((m2 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
             const Outs oo = outs(o1, o2);
             // bit 15 of sx ^ q_p = parity of #(q >= 0) over the other edges;
             // negatives among the others = (deg - 1) - that
@@ -184,7 +184,7 @@ struct PairDecoder {
                 }
             }
         }
-        return (int)(((unsat >> 15) & 1u) | ((unsat >> 30) & 2u));
+        return (int)((unsat >> 15) & 0x00010001u);
     }
 
     // large degree: the first pass leaves each edge's q'' in its message slot
@@ -212,9 +212,8 @@ struct PairDecoder {
         const unsigned dodd = (deg & 1) ? 0x80008000u : 0u;
         const unsigned unsat = (sp ^ dodd) & 0x80008000u;
         if (writeR) {
-            const unsigned d1 = m1 - pc.BETA2, d2 = m2 - pc.BETA2;
-            const unsigned o1 = ((d1 * (unsigned)pc.an) >> pc.as) & pc.amask2;
-            const unsigned o2 = ((d2 * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o1 = ((m1 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
+            const unsigned o2 = ((m2 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
             const Outs oo = outs(o1, o2);
             const unsigned sxk = sx ^ (((deg - 1) & 1) ? 0x80008000u : 0u);
 #pragma unroll 4
@@ -234,7 +233,7 @@ struct PairDecoder {
                 red_add(Pn + po, rn);
             }
         }
-        return (int)(((unsat >> 15) & 1u) | ((unsat >> 30) & 2u));
+        return (int)((unsat >> 15) & 0x00010001u);
     }
 
     // Two checks of one QC row block at once (rows r and r + dr, 16-bit
@@ -278,10 +277,10 @@ struct PairDecoder {
         const unsigned dodd = (deg & 1) ? 0x80008000u : 0u;
         const unsigned unsatA = (spA ^ dodd) & 0x80008000u, unsatB = (spB ^ dodd) & 0x80008000u;
         if (writeR) {
-            const unsigned o1A = (((m1A - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
-            const unsigned o2A = (((m2A - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
-            const unsigned o1B = (((m1B - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
-            const unsigned o2B = (((m2B - pc.BETA2) * (unsigned)pc.an) >> pc.as) & pc.amask2;
+            const unsigned o1A = ((m1A * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
+            const unsigned o2A = ((m2A * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
+            const unsigned o1B = ((m1B * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
+            const unsigned o2B = ((m2B * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
             const Outs ooA = outs(o1A, o2A), ooB = outs(o1B, o2B);
             const unsigned odd = ((deg - 1) & 1) ? 0x80008000u : 0u;
             const unsigned sxkA = sxA ^ odd, sxkB = sxB ^ odd;
@@ -302,14 +301,14 @@ struct PairDecoder {
                 red_add(Pn + poB, rnB);
             }
         }
-        return (int)(((unsatA >> 15) & 1u) | ((unsatA >> 30) & 2u) | ((unsatB >> 13) & 4u) | ((unsatB >> 28) & 8u));
+        return (int)(((unsatA >> 15) & 0x00010001u) + ((unsatB >> 15) & 0x00010001u));
     }
 
     // check pass; returns u of half 0 in the low 16 bits and half 1 above
     template <bool MASK>
     __device__ __forceinline__ int check_pass(unsigned km, unsigned kb, bool writeR, const unsigned *Pcur,
                                               unsigned *Pnext) const {
-        int u0 = 0, u1 = 0;
+        int u = 0;  // unsatisfied checks: half 0 in the low 16 bits, half 1 above
         const unsigned char *Pc = (const unsigned char *)Pcur;
         unsigned char *Pn = (unsigned char *)Pnext;
         const int Z = g.Z;
@@ -335,8 +334,7 @@ struct PairDecoder {
                                 return rjz4[p] + 4 * (int)min((unsigned)t, (unsigned)(t - Z));
                             },
                             [&](int p) { return rb + pz[p] + r * RSZ; });
-                        u0 += f & 1;
-                        u1 += f >> 1;
+                        u += f;
                     }
                 } else {
                     const int32_t *rjz = sg.rjz + i * g.dc_max;
@@ -346,8 +344,7 @@ struct PairDecoder {
                         // rows in pairs (r, r + T) while both exist
                         for (; r + gp.T < Z; r += 2 * gp.T) {
                             const int f = check_rows2<MASK>(deg, km, kb, writeR, Pc, Pn, rjz, rs, rb, r, gp.T);
-                            u0 += (f & 1) + ((f >> 2) & 1);
-                            u1 += ((f >> 1) & 1) + (f >> 3);
+                            u += f;
                         }
                     }
                     for (; r < Z; r += gp.T) {
@@ -358,8 +355,7 @@ struct PairDecoder {
                                 return 4 * (rjz[p] + (int)min((unsigned)t, (unsigned)(t - Z)));
                             },
                             [&](int p) { return rb + (p * Z + r) * RSZ; });
-                        u0 += f & 1;
-                        u1 += f >> 1;
+                        u += f;
                     }
                 }
             }
@@ -371,11 +367,10 @@ struct PairDecoder {
                 const int f = check_node<MASK>(
                     deg, km, kb, writeR, Pc, Pn, [&](int p) { return 4 * (int)sg.c_vn[e0 + p]; },
                     [&](int p) { return (p * m + c) * RSZ; });
-                u0 += f & 1;
-                u1 += f >> 1;
+                u += f;
             }
         }
-        return gp.sum(u0 | (u1 << 16));
+        return gp.sum(u);
     }
 
     __device__ __forceinline__ int vdeg(int v) const {
@@ -472,6 +467,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     pc.LO2 = (kBeta - (unsigned)pc.sat) * 0x00010001u;
     pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
+    pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
     PairDecoder<QC, DC, EXACT, I8> dec{g, sg, gp, pc, Rb};
 
     const long long total = (long long)b.ctr->n_cand_total;

@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsA
     pc.LO2 = (kBeta - (unsigned)pc.sat) * 0x00010001u;
     pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
+    pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
     PairDecoder<QC, DC, EXACT, false> dec{g, sg, gp, pc, Rb};
 
     for (int w = gp.gt; w < nw; w += gp.T) Tm[w] = 0u;
