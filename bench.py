@@ -311,12 +311,12 @@ def run_ours(args):
     peak = INT_LANES_PER_SM * N_SMS * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s
     avg_dec_ms = sum(ms_dec) / len(ms_dec)
     # DRAM bytes (read + write) of one decode launch: an ncu capture of this kernel on the PEG
-    # workload's first 40,000 candidates read 724,992 B and wrote none (candidate sets in, records
+    # workload's first 40,000 candidates read 725,504 B and wrote none (candidate sets in, records
     # out, both proportional to the candidates), scaled to the launch's candidates
     traffic, traffic_note = None, "not captured for this workload"
     if args.workload == "peg1008" and args.decoder == "nms16":
-        traffic = 724992.0 / 40000 * float(s["n_cand"])
-        traffic_note = "scaled by candidates from an ncu capture of the first 40,000 (724,992 B)"
+        traffic = 725504.0 / 40000 * float(s["n_cand"])
+        traffic_note = "scaled by candidates from an ncu capture of the first 40,000 (725,504 B)"
 
     eu_per_step = eu / args.steps
     achieved = ALG_OPS_PER_EDGE * eu_per_step / (avg_dec_ms / 1e3) / 1e12
