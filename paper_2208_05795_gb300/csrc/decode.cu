@@ -8,6 +8,8 @@ namespace tsx {
 // per-decoder translation units
 cudaError_t launch_nms16(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, bool pair,
                          cudaStream_t);
+cudaError_t launch_nms16_vn(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &,
+                            cudaStream_t);
 cudaError_t launch_nms8(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, bool pair,
                         cudaStream_t);
 cudaError_t launch_spa(const DevCode &, const DecodeParams &, const EnumBuffers &, const LaunchShape &, cudaStream_t);
@@ -20,14 +22,14 @@ cudaError_t launch_batch8(const BatchArgs &, int, bool qc, int dc_max, bool reg6
 
 namespace {
 
-enum { kLayScalar = 0, kLayPair = 1, kLaySieve = 2, kLayIs = 3 };
+enum { kLayScalar = 0, kLayPair = 1, kLaySieve = 2, kLayIs = 3, kLayPairVn = 4 };
 
 int msg_bytes(int decoder) { return decoder == TSX_DEC_NMS_I8 ? 1 : (decoder == TSX_DEC_SPA_F32 ? 4 : 2); }
 int post_bytes(int decoder) { return decoder == TSX_DEC_SPA_F32 ? 4 : 2; }
 
 SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
     SlotLayout L{};
-    L.tables_bytes = al16(tab_offsets(g, kind == kLayPair || kind == kLayIs).total);
+    L.tables_bytes = al16(tab_offsets(g, kind == kLayPair || kind == kLayIs || kind == kLayPairVn).total);
     const int nw = (g.n + 31) / 32;
     // message slots: QC edges, or the position-major m x dc_max grid of a CSR code
     const int nmsg = g.kind == TSX_CODE_QC ? g.E : g.m * g.dc_max;
@@ -42,6 +44,12 @@ SlotLayout make_layout(const DevCode &g, int decoder, int kind) {
         const int xstride = (nw + 3) & ~3;
         L.r_off = x; x += al16(nmsg * rsz);
         L.p_off = x; x += al16(2 * g.n * 4);  // current and accumulating posteriors
+        L.xa_off = x; x += al16(4 * xstride * 4);
+        L.xb_off = L.xa_off;
+    } else if (kind == kLayPairVn) {
+        const int xstride = (nw + 3) & ~3;
+        L.r_off = x; x += al16(nmsg * 4);
+        L.p_off = x; x += al16(g.n * 4);  // one posterior buffer, rebuilt by the variable-node pass
         L.xa_off = x; x += al16(4 * xstride * 4);
         L.xb_off = L.xa_off;
     } else if (kind == kLayIs) {
@@ -121,6 +129,10 @@ cudaError_t launch_decode(const DevCode &g, const DecodeParams &dp, const EnumBu
     // the two-codeword kernel where its bounds hold and its layout fits a CTA
     const bool pair = !force_scalar && pair_ok(g, dp) && plan(g, dp.decoder, kLayPair, G, groups, ctas_per_sm,
                                                              num_sms, &sh, kPairWarps);
+    // QC codes of large check degree whose two-buffer layout does not fit: the variable-node-pass form
+    if (!pair && !force_scalar && pair_ok(g, dp) && g.kind == TSX_CODE_QC && dp.decoder == TSX_DEC_NMS_I16 &&
+        g.dc_max > 8 && plan(g, dp.decoder, kLayPairVn, G, groups, ctas_per_sm, num_sms, &sh, kPairWarps))
+        return launch_nms16_vn(g, dp, b, sh, st);
     if (!pair && !plan(g, dp.decoder, kLayScalar, G, groups, ctas_per_sm, num_sms, &sh))
         return cudaErrorInvalidConfiguration;
     switch (dp.decoder) {

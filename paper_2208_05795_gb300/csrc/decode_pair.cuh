@@ -76,7 +76,11 @@ struct Half {
     __device__ __forceinline__ int Ik(int t) const { return t == 0 ? I0 : t == 1 ? I1 : t == 2 ? I2 : I3; }
 };
 
-template <bool QC, int DC, bool EXACT, bool I8>
+// VN: the variable-node-pass form (QC codes): one posterior buffer, rebuilt
+// after each check pass from the stored messages, instead of the
+// accumulating second buffer -- 4 bytes per node less, for codes whose
+// two-buffer layout does not fit a CTA.
+template <bool QC, int DC, bool EXACT, bool I8, bool VN = false>
 struct PairDecoder {
     static constexpr int RSZ = I8 ? 2 : 4;  // bytes of one packed message pair
     const DevCode &g;
@@ -180,7 +184,7 @@ struct PairDecoder {
                 if (EXACT || p < deg) {
                     const unsigned rn = edge_out(qs[p], as_[p], m1, oo, sxk);
                     stR(re(p), rn);
-                    red_add(Pn + po[p], rn);
+                    if constexpr (!VN) red_add(Pn + po[p], rn);
                 }
             }
         }
@@ -230,7 +234,7 @@ struct PairDecoder {
                 }
                 const unsigned rn = edge_out(q, a, m1, oo, sxk);
                 stR(ro, rn);
-                red_add(Pn + po, rn);
+                if constexpr (!VN) red_add(Pn + po, rn);
             }
         }
         return (int)((unsat >> 15) & 0x00010001u);
@@ -297,8 +301,10 @@ struct PairDecoder {
                 const unsigned rnB = edge_out(qB, aB, m1B, ooB, sxkB);
                 stR(roA, rnA);
                 stR(roB, rnB);
-                red_add(Pn + poA, rnA);
-                red_add(Pn + poB, rnB);
+                if constexpr (!VN) {
+                    red_add(Pn + poA, rnA);
+                    red_add(Pn + poB, rnB);
+                }
             }
         }
         return (int)(((unsatA >> 15) & 0x00010001u) + ((unsatB >> 15) & 0x00010001u));
@@ -413,6 +419,34 @@ struct PairDecoder {
     __device__ __forceinline__ static void set_half(unsigned *P, int v, int h, unsigned val) {
         ((uint16_t *)P)[2 * v + h] = (uint16_t)val;
     }
+    __device__ __forceinline__ static void add_half(unsigned *P, int v, int h, int delta) {
+        uint16_t *q = (uint16_t *)P + 2 * v + h;
+        *q = (uint16_t)(*q + delta);
+    }
+
+    // the variable-node pass of the VN form (QC): P'(v) = L + beta - dv B +
+    // sum of the R' of v's edges in both halves -- the value the accumulating
+    // form builds with red.add -- for the baseline channel value L (impulse
+    // nodes are corrected afterwards)
+    __device__ __forceinline__ void vn_pass(unsigned *P, int Lb) const {
+        const int Z = g.Z;
+        for (int j = 0; j < g.n_b; j++) {
+            const int dv = sg.cdeg[j];
+            const unsigned l = (unsigned)(Lb + (int)kBeta - dv * pc.B);
+            const unsigned l2 = l | (l << 16);
+            const int32_t *eo = sg.ceoff + j * g.dv_max;
+            const int16_t *sh = sg.cs + j * g.dv_max;
+            for (int k = gp.gt; k < Z; k += gp.T) {
+                unsigned acc = l2;
+                for (int t = 0; t < dv; t++) {
+                    // block (i, j) with shift s joins row r to column (r + s) mod Z: r = (k - s) mod Z
+                    const int r = wrapZneg(k - sh[t], Z);
+                    acc += ldR((eo[t] + r) * RSZ);
+                }
+                P[j * Z + k] = acc;
+            }
+        }
+    }
 
     // x_k of half h (P < 0, i.e. bit 15 of the half clear) into a bitmask
     __device__ __forceinline__ void save_x(const unsigned *P, int h, uint32_t *xw) const {
@@ -436,7 +470,7 @@ struct PairDecoder {
 
 // The decode loop of one group (G warps, group index grp) over the
 // candidate queue of one code; the code's tables are already in sg.
-template <bool QC, int DC, bool EXACT, bool I8>
+template <bool QC, int DC, bool EXACT, bool I8, bool VN = false>
 __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, const SlotLayout &lay,
                          int G, const SGraph &sg, unsigned char *smem, int grp) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -451,7 +485,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     gp.bar = 1 + grp;
     gp.red = misc->red;
     unsigned char *Rb = slot + lay.r_off;
-    unsigned *Pbuf = (unsigned *)(slot + lay.p_off);  // [2][n]
+    unsigned *Pbuf = (unsigned *)(slot + lay.p_off);  // [2][n] ([n] in the VN form)
     const int nw = (g.n + 31) >> 5;
     uint32_t *xb = (uint32_t *)(slot + lay.xa_off);  // 4 buffers of nw words: [half][cur/keep]
     const int xstride = (nw + 3) & ~3;
@@ -468,7 +502,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
-    PairDecoder<QC, DC, EXACT, I8> dec{g, sg, gp, pc, Rb};
+    PairDecoder<QC, DC, EXACT, I8, VN> dec{g, sg, gp, pc, Rb};
 
     const long long total = (long long)b.ctr->n_cand_total;
     const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
@@ -561,21 +595,34 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         }
     };
 
+    // VN form: the impulse nodes of half hh after a variable-node pass (built
+    // with the baseline L), or of a new decode
+    auto patch_vn = [&](Half &h, int hh, unsigned *Pc, bool fresh) {
+        if (h.idx >= 0 && gp.gt < h.nI) {
+            const int t = h.Ik(gp.gt);
+            if (fresh) dec.set_half(Pc, t, hh, (unsigned)(h.Limp + (int)kBeta));
+            else dec.add_half(Pc, t, hh, h.Limp - Lb);
+        }
+    };
+
     {
         unsigned *Pc = Pbuf, *Pn = Pbuf + g.n;
-        dec.init_accum(Pn, Lb);
+        if constexpr (!VN) dec.init_accum(Pn, Lb);
         for (int hh = 0; hh < 2; hh++) {
             fetch(H[hh]);
             settle(H[hh], hh);
             start_cur(H[hh], hh, Pc);  // idle halves too: every word stays a valid decode state
         }
         gp.sync();
-        for (int hh = 0; hh < 2; hh++) patch(H[hh], hh, Pc, Pn, true);
+        for (int hh = 0; hh < 2; hh++) {
+            if constexpr (VN) patch_vn(H[hh], hh, Pc, true);
+            else patch(H[hh], hh, Pc, Pn, true);
+        }
         gp.sync();
     }
 
     while (H[0].idx >= 0 || H[1].idx >= 0) {
-        unsigned *Pc = Pbuf + pcur * g.n, *Pn = Pbuf + (pcur ^ 1) * g.n;
+        unsigned *Pc = VN ? Pbuf : Pbuf + pcur * g.n, *Pn = VN ? Pbuf : Pbuf + (pcur ^ 1) * g.n;
         const unsigned km = (H[0].first ? 0xFFFF0000u : 0xFFFFFFFFu) & (H[1].first ? 0x0000FFFFu : 0xFFFFFFFFu);
         const unsigned kb = pc.B2 & ~km;
         const bool wr = (H[0].idx >= 0 && H[0].k < dp.K) || (H[1].idx >= 0 && H[1].k < dp.K);
@@ -628,6 +675,27 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
             }
             restart[hh] = 1;
         }
+        if constexpr (VN) {
+            // P_{k+1} from the messages just written, in place of P_k
+            gp.sync();
+            if (wr) {
+                dec.vn_pass(Pc, Lb);
+                gp.sync();
+            }
+            for (int hh = 0; hh < 2; hh++) {
+                Half &h = H[hh];
+                if (restart[hh]) {
+                    if (settle(h, hh)) start_cur(h, hh, Pc);
+                } else if (h.idx >= 0) {
+                    h.k++;
+                    h.first = 0;
+                }
+            }
+            gp.sync();
+            for (int hh = 0; hh < 2; hh++) patch_vn(H[hh], hh, Pc, restart[hh] != 0);
+            gp.sync();
+            continue;
+        }
         // Pn (= P_{k+1}) becomes current; the old Pc becomes the next accumulator
         gp.sync();
         for (int hh = 0; hh < 2; hh++) {
@@ -659,6 +727,16 @@ __global__ void __launch_bounds__(32 * kPairWarps) pair_kernel(DevCode g, Decode
     const SGraph sg = load_tables(g, smem, true);
     __syncthreads();
     pair_run<QC, DC, EXACT, I8>(g, dp, b, lay, G, sg, smem, (threadIdx.x >> 5) / G);
+}
+
+// the VN form for QC codes of large check degree whose two-buffer layout does not fit
+template <bool I8>
+__global__ void __launch_bounds__(32 * kPairWarps) pair_vn_kernel(DevCode g, DecodeParams dp, EnumBuffers b,
+                                                               SlotLayout lay, int G) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SGraph sg = load_tables(g, smem, true);
+    __syncthreads();
+    pair_run<true, 32, false, I8, true>(g, dp, b, lay, G, sg, smem, (threadIdx.x >> 5) / G);
 }
 
 // One persistent launch over several codes: every CTA works through the

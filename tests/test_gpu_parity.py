@@ -300,3 +300,27 @@ def test_qc2640_full_size_sampled(qc2640):
     # the 8-cycle sets of size 4 are present
     assert (v["cand_vars"][:, 3] >= 0).sum() > 0
     _ts_invariants(g, v, qc=True)
+
+
+def test_large_qc_code_variable_node_form_sampled():
+    # n = 11520 (4 x 30 base, Z = 384, check degree up to 28): the two-buffer
+    # layout of the two-codeword kernel does not fit a CTA, so the decode runs
+    # its variable-node-pass form; sampled candidates against the oracle
+    code = synth.batch_codes([122])[0]
+    w = dict(code=code, K=20, base_llr=16, amp_steps=10, max_size=2, cycle_len=0)
+    v = run_lib(code, cand_end=3000, **_params(w))
+    assert len(v["cand_thr"]) == 3000
+    rows = np.concatenate([(v["cand_vars"] >= 0).sum(1, keepdims=True), v["cand_vars"]], axis=1)
+    rng = np.random.default_rng(3)
+    pick = np.sort(rng.choice(len(rows), 30, replace=False))
+    g = oracle.Graph(code)
+    res = g.enumerate(rows[pick], **_params(w))
+    assert (res.thr >= 0).any()
+    for j, i in enumerate(pick):
+        assert int(v["cand_thr"][i]) == int(res.thr[j]), rows[i]
+        assert int(v["cand_decodes"][i]) == int(res.decodes[j]), rows[i]
+        assert int(v["cand_iters"][i]) == int(res.iters[j]), rows[i]
+        ts = int(v["cand_ts"][i])
+        lkey = v["keys"][ts] if ts >= 0 else None
+        okey = res.ts_list[res.ts[j]].key if res.ts[j] >= 0 else None
+        assert lkey == okey, rows[i]
