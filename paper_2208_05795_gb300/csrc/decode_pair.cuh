@@ -318,7 +318,25 @@ struct PairDecoder {
         const unsigned char *Pc = (const unsigned char *)Pcur;
         unsigned char *Pn = (unsigned char *)Pnext;
         const int Z = g.Z;
-        if constexpr (QC) {
+        if constexpr (QC && VN) {
+            // all row blocks at once (check c = i Z + r), so that a group may be wider than Z rows
+            const unsigned zm = Z > 1 ? 0xFFFFFFFFu / (unsigned)Z + 1u : 0u;  // c / Z = umulhi(c, zm), c < 2^16
+            for (int c = gp.gt; c < g.m; c += gp.T) {
+                const int i = Z > 1 ? (int)__umulhi((unsigned)c, zm) : c;
+                const int r = c - i * Z;
+                const int deg = sg.rdeg[i];
+                const int rb = sg.reoff[i] * RSZ;
+                const int32_t *rjz = sg.rjz + i * g.dc_max;
+                const int16_t *rs = sg.rs + i * g.dc_max;
+                u += check_node<MASK>(
+                    deg, km, kb, writeR, Pc, Pn,
+                    [&](int p) {
+                        const int t = r + rs[p];
+                        return 4 * (rjz[p] + (int)min((unsigned)t, (unsigned)(t - Z)));
+                    },
+                    [&](int p) { return rb + (p * Z + r) * RSZ; });
+            }
+        } else if constexpr (QC) {
             for (int i = 0; i < g.m_b; i++) {
                 const int deg = EXACT ? DC : sg.rdeg[i];
                 const int rb = sg.reoff[i] * RSZ;
@@ -430,21 +448,21 @@ struct PairDecoder {
     // nodes are corrected afterwards)
     __device__ __forceinline__ void vn_pass(unsigned *P, int Lb) const {
         const int Z = g.Z;
-        for (int j = 0; j < g.n_b; j++) {
+        const unsigned zm = Z > 1 ? 0xFFFFFFFFu / (unsigned)Z + 1u : 0u;  // v / Z = umulhi(v, zm), v < 2^15
+        for (int v = gp.gt; v < g.n; v += gp.T) {
+            const int j = Z > 1 ? (int)__umulhi((unsigned)v, zm) : v;
+            const int k = v - j * Z;
             const int dv = sg.cdeg[j];
-            const unsigned l = (unsigned)(Lb + (int)kBeta - dv * pc.B);
-            const unsigned l2 = l | (l << 16);
             const int32_t *eo = sg.ceoff + j * g.dv_max;
             const int16_t *sh = sg.cs + j * g.dv_max;
-            for (int k = gp.gt; k < Z; k += gp.T) {
-                unsigned acc = l2;
-                for (int t = 0; t < dv; t++) {
-                    // block (i, j) with shift s joins row r to column (r + s) mod Z: r = (k - s) mod Z
-                    const int r = wrapZneg(k - sh[t], Z);
-                    acc += ldR((eo[t] + r) * RSZ);
-                }
-                P[j * Z + k] = acc;
+            const unsigned l = (unsigned)(Lb + (int)kBeta - dv * pc.B);
+            unsigned acc = l | (l << 16);
+            for (int t = 0; t < dv; t++) {
+                // block (i, j) with shift s joins row r to column (r + s) mod Z: r = (k - s) mod Z
+                const int r = wrapZneg(k - sh[t], Z);
+                acc += ldR((eo[t] + r) * RSZ);
             }
+            P[v] = acc;
         }
     }
 
