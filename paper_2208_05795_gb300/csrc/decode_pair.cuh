@@ -13,8 +13,8 @@
 //   message   R' = r + B                     B = 1024 (int16) / 128 (int8)
 //   posterior P' = P + beta                  beta = 0x8000
 //   channel   L'(v) = L_v + beta - dv(v) B   so P' = L' + sum_c R'
-//   extrinsic q' = P' - R' = q + beta - B    clamped to [beta - B - sat, beta - B + sat]
-//   then q'' = q' + B = clamp(q) + beta: bit 15 of each half is [q >= 0]
+//   extrinsic q'' = clamp(P' - R' + B) = clamp(q) + beta, clamped to [beta - sat, beta + sat]
+//                                           (one three-input add, then min/max): bit 15 of each half is [q >= 0]
 //   magnitude a = max(q'', 2 beta - q'') = |q| + beta   (2 beta - x = ~x + 1 per half)
 // Every intermediate stays inside [0, 0xFFFF] per half for rmax <= B and
 // (dv + 2) sat <= beta - B, which the launcher checks; both halves always
@@ -26,6 +26,12 @@
 // No variable-node pass: each check adds its new messages into the next
 // posterior buffer with shared-memory atomic adds (exact and order-free on
 // the biased words); that buffer starts at L' with the impulse values in it.
+// For QC codes whose two buffers do not fit a CTA, the variable-node-pass
+// form (VN) keeps one buffer and rebuilds it from the messages after each
+// check pass; it gives the same words.
+//
+// The first check pass of a decode reads the zero message B in its half; a
+// check pass in which no half starts a decode skips that masking.
 #pragma once
 #include "decode_impl.cuh"
 
