@@ -186,7 +186,6 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload_for(args.workload, 0)
-    base, _ = cpu_baseline(w, args.decoder, max(2.0, args.cpu_seconds / 3))
     times, eus = [], []
     import oracle
     g = oracle.Graph(w["code"])

@@ -1,0 +1,54 @@
+"""CPU checks of bench.py: the reference arm (the oracle timed on host cores)
+prints one JSON line with the keys of the benchmark contract, and the
+synthetic workloads are built as their recipes state (seeded, with the
+stated sizes), without a GPU."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+        "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e")
+
+
+def test_reference_arm_prints_one_contract_line():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "qc96", "--steps", "2",
+                        "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.strip().splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in KEYS:
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["config"]["workload"] == "qc96"
+
+
+def test_serving_stream_recipe():
+    codes, jobs = bench.serve_jobs(200)
+    assert len(codes) == 8 and all(c.n <= 10_000 for c in codes)
+    kinds = [j[0] for j in jobs]
+    assert 0.6 < kinds.count("enum") / len(jobs) < 0.9
+    for kind, c, p in jobs:
+        assert 0 <= c < len(codes)
+        if kind == "enum":
+            assert 1_000 <= p["cand_end"] <= 100_000 and p["max_size"] == 2
+        else:
+            assert p["n_samples"] == 1_000_000 and 3.0 <= p["ebn0_db"] <= 5.0
+    # seeded: the same stream twice
+    assert bench.serve_jobs(200)[1] == jobs
+
+
+def test_batch_workload_recipe():
+    w = bench.workload_for("batch32", 0)
+    assert w["code"].name == "batch100" and w["max_size"] == 2 and w["K"] == 20
+    shifts = w["code"].shifts
+    assert shifts.shape[0] == 4 and 16 <= shifts.shape[1] <= 32
+    assert np.all(shifts < w["code"].Z)
