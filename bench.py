@@ -54,6 +54,11 @@ ALG_OPS_PER_EDGE = 12
 INT_LANES_PER_SM = 128
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
+try:  # the maximum SM clock measured on this machine, when the measurement file is present
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
+        SM_MAX_MHZ = float(json.load(_f).get("sm_max_mhz", SM_MAX_MHZ))
+except (OSError, ValueError):
+    pass
 
 
 def parse():
