@@ -127,7 +127,12 @@ typedef struct {
     int32_t warps_per_cta; /* warps per codeword group (0 = automatic) */
     int32_t ctas_per_sm;   /* 0 = as many as are resident */
     int32_t kernel;        /* min-sum kernel: 0 automatic, 1 one codeword per group,
-                              2 two codewords per lane (16-bit halves) */
+                              2 two codewords per lane (16-bit halves).  Automatic and 2 use
+                              two codewords per lane where its 16-bit bounds hold and its
+                              layout fits a CTA (for int16 QC codes of check degree > 8 whose
+                              two posterior buffers do not fit: one buffer rebuilt by a
+                              variable-node pass), else one codeword per group; the results
+                              are the same */
 } tsx_enum_params;
 
 /* Fills `p` with the defaults: NMS int16, K=20, base 16, sat 511, alpha 3/4,
