@@ -52,3 +52,11 @@ def test_batch_workload_recipe():
     shifts = w["code"].shifts
     assert shifts.shape[0] == 4 and 16 <= shifts.shape[1] <= 32
     assert np.all(shifts < w["code"].Z)
+
+
+def test_served_launch_count():
+    jobs = [("enum", 0, dict(cand_end=40_000)), ("is", 1, dict(n_samples=1_000_000)),
+            ("enum", 2, dict(cand_end=1_000))]
+    res = [{"enum_stats": {"n_cand": 40_000}}, {"enum_stats": {"n_cand": 0}}, {"enum_stats": {"n_cand": 700}}]
+    # 3 + ceil(40000/16384) + 3 = 9; ceil(10^6/32768) + 2 = 33; 3 + 1 + 3 = 7
+    assert bench.served_launches(jobs, res) == 9 + 33 + 7
