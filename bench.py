@@ -593,6 +593,7 @@ def run_serve(args):
         out[mode] = (res, st, clk.summary())
     rp, sp, _ = out["plain"]
     rs, ss, clocks = out["served"]
+    launches = served_launches(jobs, rs)
     same = all(a["status"] == b["status"] == 0 and
                (a["enum_stats"]["n_ts"], a["enum_stats"]["decodes"], a["is_result"]["sum_w"],
                 a["is_result"]["n_fail"]) ==
@@ -630,10 +631,27 @@ def run_serve(args):
         "cpu_baseline": None,
         "e2e": {"value": ss["p99_ms"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                 "note": "latency is measured from submit (host) to results copied to host memory"},
-        "gpu_launches": None,
+        "gpu_launches": launches,
+        "gpu_launches_note": "served mode, counted from each job's candidates or samples and the server's "
+                             "chunk sizes (candidate bound taken as the canonical count: a lower bound)",
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+
+
+def served_launches(jobs, results, chunk_candidates=16384, chunk_samples=32768):
+    """Kernel launches of the served stream: an enumeration job runs the
+    candidate kernels (count, scan, write), one decode launch per chunk of
+    candidates, the sieve and two compaction kernels; an importance-sampling
+    job one sampling launch per chunk of samples and two reductions."""
+    n = 0
+    for (kind, _, p), r in zip(jobs, results):
+        if kind == "enum":
+            cands = max(1, int(r["enum_stats"]["n_cand"]))
+            n += 3 + -(-cands // chunk_candidates) + 1 + 2
+        else:
+            n += -(-int(p["n_samples"]) // chunk_samples) + 2
+    return n
 
 
 def isfer_setup(tsx, stream=None):
