@@ -56,7 +56,7 @@ class _IsParams(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("decoder", C.c_int), ("K", C.c_int), ("base_llr", C.c_int), ("sat", C.c_int),
                 ("alpha_num", C.c_int), ("alpha_shift", C.c_int), ("amp_steps", C.c_int),
-                ("spa_clip", C.c_float), ("spa_amax", C.c_float)]
+                ("spa_clip", C.c_float), ("spa_amax", C.c_float), ("list_mode", C.c_int), ("kstart", C.c_int)]
 
 
 def lib():
@@ -90,7 +90,7 @@ def lib():
             L.og_cands_copy.argtypes = [vp, I32P]
             L.og_cands_free.argtypes = [vp]
             L.og_decode_nms.argtypes = [vp, I32P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                        U8P, C.POINTER(C.c_int), I32P, I32P]
+                                        U8P, C.POINTER(C.c_int), I32P, I32P, vp]
             L.og_decode_nms.restype = C.c_int
             L.og_decode_spa.argtypes = [vp, F32P, C.c_int, C.c_float, C.c_int, U8P,
                                         C.POINTER(C.c_int), I32P]
@@ -173,7 +173,7 @@ class TS:
     count: int
     thr: int
     thr_f: float
-    kind: int  # 1 = Tree(X), 2 = Tree(TS(X))
+    kind: int  # 1 = Tree(X), 2 = Tree(TS(X)); list mode: 3 = both
 
 
 @dataclass
@@ -249,15 +249,19 @@ class Graph:
         return out
 
     # --- decoders -------------------------------------------------------
-    def decode_nms(self, Lv, K, sat=511, alpha_num=3, alpha_shift=2, wstart=None):
+    def decode_nms(self, Lv, K, sat=511, alpha_num=3, alpha_shift=2, wstart=None, trace=False):
         Lv = np.ascontiguousarray(np.asarray(Lv, dtype=np.int32))
         ws = max(1, self.girth() // 2) if wstart is None else wstart
         xb = np.zeros(self.n, dtype=np.uint8)
         kl = C.c_int()
         ut = np.zeros(K + 1, dtype=np.int32)
         P = np.zeros(self.n, dtype=np.int32)
-        f = lib().og_decode_nms(self.h, Lv, K, sat, alpha_num, alpha_shift, ws, xb, C.byref(kl), ut, P)
+        xt = np.zeros((K + 1, self.n), dtype=np.uint8) if trace else None
+        f = lib().og_decode_nms(self.h, Lv, K, sat, alpha_num, alpha_shift, ws, xb, C.byref(kl), ut, P,
+                                xt.ctypes.data_as(C.c_void_p) if trace else None)
         self.last_P = P
+        # with trace, self.last_trace[k] = x_k for k = 0..K_last
+        self.last_trace = xt[: kl.value + 1] if trace else None
         return bool(f), xb, kl.value, ut[: kl.value + 1]
 
     def decode_spa(self, Lv, K, clip=30.0, wstart=None):
@@ -319,12 +323,17 @@ class Graph:
     # --- the whole method -----------------------------------------------
     def enumerate(self, cands=None, *, decoder="nms", K=20, base_llr=16, sat=511, alpha_num=3,
                   alpha_shift=2, amp_steps=10, spa_clip=30.0, spa_amax=64.0, max_size=3,
-                  cycle_len=0) -> Enumeration:
+                  cycle_len=0, list_mode=False, kstart=0) -> Enumeration:
+        """list_mode (min-sum): every non-empty set of the ordered list S1(x_k),
+        S2(x_k), k = kstart (0: floor(girth/2)) .. K_last, of the decode at the
+        threshold is a trapping set; per trapping set, count = candidates whose
+        list holds it and kind = 1 (S1), 2 (S2) or 3 (both); the per-candidate
+        ts index is -1 in this mode."""
         if cands is None:
             cands = self.candidates(max_size, cycle_len)
         cands = np.ascontiguousarray(np.asarray(cands, dtype=np.int32).reshape(-1, 5))
         p = _Params(0 if decoder == "nms" else 1, K, base_llr, sat, alpha_num, alpha_shift,
-                    amp_steps, spa_clip, spa_amax)
+                    amp_steps, spa_clip, spa_amax, 1 if list_mode else 0, kstart)
         L = lib()
         h = L.og_enumerate(self.h, C.byref(p), cands, cands.shape[0])
         N = cands.shape[0]

@@ -356,10 +356,12 @@ static int unsat_count(const og_graph *g, const unsigned char *x) {
  * Best error pattern (Sec. III, S(min_iter w_H(H x_iter)) with the list
  * starting at x_{floor(girth/2)}): x* = x_k for the first k in
  * [wstart, K_last] with minimal u_k; if K_last < wstart, x* = x_{K_last}.
- * Returns 1 if the decoder failed (x_{K_last} != 0), else 0. */
+ * Returns 1 if the decoder failed (x_{K_last} != 0), else 0.  x_trace, when
+ * given, receives every x_k, k = 0..K_last. */
 int og_decode_nms(const og_graph *g, const int *L, int K, int sat, int an, int as, int wstart,
                   unsigned char *xbest, int *K_last, int *u_trace /* K+1 or NULL */,
-                  int *P_out /* n or NULL: P_v after the last iteration run */) {
+                  int *P_out /* n or NULL: P_v after the last iteration run */,
+                  unsigned char *x_trace /* (K+1) x n or NULL: x_k in row k */) {
     int E = g->m * g->dcmax;
     int *q = (int *)malloc(sizeof(int) * E), *r = (int *)malloc(sizeof(int) * E);
     unsigned char *x = (unsigned char *)malloc(g->n);
@@ -371,6 +373,7 @@ int og_decode_nms(const og_graph *g, const int *L, int K, int sat, int an, int a
     }
     int u = unsat_count(g, x), ubest = 1 << 30, kl = 0;
     if (u_trace) u_trace[0] = u;
+    if (x_trace) memcpy(x_trace, x, g->n);
     for (int k = 1; k <= K && u != 0; k++) {
         for (int c = 0; c < g->m; c++) {
             int d = g->cdeg[c];
@@ -400,6 +403,7 @@ int og_decode_nms(const og_graph *g, const int *L, int K, int sat, int an, int a
         }
         u = unsat_count(g, x);
         if (u_trace) u_trace[k] = u;
+        if (x_trace) memcpy(x_trace + (size_t)k * g->n, x, g->n);
         kl = k;
         if (k >= wstart && u < ubest) { ubest = u; memcpy(xbest, x, g->n); }
     }
@@ -677,6 +681,8 @@ typedef struct {
     int amp_steps;  /* s */
     float spa_clip; /* sum-product clip */
     float spa_amax; /* sum-product: amplitude range in LLR units */
+    int list_mode;  /* 1: every set of the ordered list S1(x_k), S2(x_k), k = kstart..K_last */
+    int kstart;     /* first iteration of that list; 0 = floor(girth / 2) (at least 1) */
 } og_params;
 
 typedef struct {
@@ -728,33 +734,46 @@ og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* nc
     R->which = (int *)malloc(sizeof(int) * ncand);
     R->decodes = (int *)malloc(sizeof(int) * ncand);
     R->iters = (int *)malloc(sizeof(int) * ncand);
-    ts_hit *hits = (ts_hit *)malloc(sizeof(ts_hit) * (ncand ? ncand : 1));
+    ts_hit *hits = (ts_hit *)malloc(sizeof(ts_hit) * (ncand ? ncand : 1));  /* grows in list mode */
     size_t nh = 0;
     int *Li = (int *)malloc(sizeof(int) * g->n);
     float *Lf = (float *)malloc(sizeof(float) * g->n);
     unsigned char *xb = (unsigned char *)malloc(g->n), *keep = (unsigned char *)malloc(g->n);
     unsigned char *T = (unsigned char *)malloc(g->n);
     int *tv = (int *)malloc(sizeof(int) * g->n);
+    /* ordered-list mode (min-sum only): the x_k of the decode at the threshold */
+    const int list = pp->list_mode && pp->decoder == 0;
+    const int ks = pp->kstart > 0 ? pp->kstart : wstart;
+    unsigned char *trace = list ? (unsigned char *)malloc((size_t)(pp->K + 1) * g->n) : NULL;
+    unsigned char *trace_keep = list ? (unsigned char *)malloc((size_t)(pp->K + 1) * g->n) : NULL;
+    unsigned char *X = (unsigned char *)malloc(g->n);
+    size_t hcap = ncand ? ncand : 1;
     for (size_t ci = 0; ci < ncand; ci++) {
         int nI = cands[5 * ci];
         const int *I = cands + 5 * ci + 1;
-        int decodes = 0, iters = 0, kl, failed = 0;
+        int decodes = 0, iters = 0, kl, failed = 0, kl_keep = 0;
         int thr = -1;
         float thr_f = -1.0f;
         if (pp->decoder == 0) {
             int lo = 0, hi = (1 << pp->amp_steps) - 1;
             for (int v = 0; v < g->n; v++) Li[v] = clampi(pp->base_llr, -pp->sat, pp->sat);
             for (int t = 0; t < nI; t++) Li[I[t]] = clampi(pp->base_llr - hi, -pp->sat, pp->sat);
-            int f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL, NULL);
+            int f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL, NULL,
+                                  list ? trace : NULL);
             decodes++; iters += kl;
             if (f) {
                 failed = 1; memcpy(keep, xb, g->n);
+                if (list) { memcpy(trace_keep, trace, (size_t)(kl + 1) * g->n); kl_keep = kl; }
                 for (int st = 0; st < pp->amp_steps && hi - lo > 1; st++) {
                     int mid = (lo + hi) >> 1;
                     for (int t = 0; t < nI; t++) Li[I[t]] = clampi(pp->base_llr - mid, -pp->sat, pp->sat);
-                    f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL, NULL);
+                    f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL,
+                                      NULL, list ? trace : NULL);
                     decodes++; iters += kl;
-                    if (f) { hi = mid; memcpy(keep, xb, g->n); } else lo = mid;
+                    if (f) {
+                        hi = mid; memcpy(keep, xb, g->n);
+                        if (list) { memcpy(trace_keep, trace, (size_t)(kl + 1) * g->n); kl_keep = kl; }
+                    } else lo = mid;
                 }
                 thr = hi;
             }
@@ -782,6 +801,35 @@ og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* nc
         if (!failed) continue;
         int which = og_extract(g, keep, I, nI, T);
         R->which[ci] = which;
+        if (list) {
+            /* Sec. III, ordered list: S1(x_k), S2(x_k) for k = kstart..K_last with
+             * X_k = supp(x_k) cup I, S1 = Tree(X_k), S2 = Tree(TS(X_k)); every
+             * non-empty element is a trapping set (counted once per candidate) */
+            size_t first = nh;
+            for (int k = ks; k <= kl_keep; k++) {
+                memcpy(X, trace_keep + (size_t)k * g->n, g->n);
+                for (int t = 0; t < nI; t++) X[I[t]] = 1;
+                for (int part = 1; part <= 2; part++) {
+                    if (part == 1) { memcpy(T, X, g->n); og_tree(g, T); }
+                    else { og_ts_closure(g, X, T); og_tree(g, T); }
+                    int a = 0, b, el;
+                    for (int v = 0; v < g->n; v++) if (T[v]) tv[a++] = v;
+                    if (!a) continue;
+                    og_classify(g, T, &a, &b, &el);
+                    int *key = (int *)malloc(sizeof(int) * a);
+                    int orbit = og_canon(g, tv, a, key);
+                    size_t dup = nh;
+                    for (size_t q = first; q < nh; q++)
+                        if (hits[q].a == a && !memcmp(hits[q].key, key, sizeof(int) * a)) { dup = q; break; }
+                    if (dup < nh) { hits[dup].kind |= part; free(key); continue; }
+                    if (nh == hcap) { hcap *= 2; hits = (ts_hit *)realloc(hits, sizeof(ts_hit) * hcap); }
+                    ts_hit *h = &hits[nh++];
+                    h->a = a; h->b = b; h->elem = el; h->kind = part; h->thr = thr; h->thr_f = thr_f;
+                    h->cand = (int)ci; h->key = key; h->orbit = orbit;
+                }
+            }
+            continue;
+        }
         if (!which) continue;
         int a = 0, b, el;
         for (int v = 0; v < g->n; v++) if (T[v]) tv[a++] = v;
@@ -808,7 +856,8 @@ og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* nc
         t->count++;
         if (hits[i].thr < t->thr) t->thr = hits[i].thr;
         if (hits[i].thr_f < t->thr_f) t->thr_f = hits[i].thr_f;
-        R->ts[hits[i].cand] = nts - 1;
+        if (list) t->kind |= hits[i].kind;
+        else R->ts[hits[i].cand] = nts - 1;
     }
     for (size_t i = 0, k = 0; i < nh; i++) { /* free the keys not kept in the list */
         if (k < (size_t)nts && R->list[k].key == hits[i].key) { k++; continue; }
@@ -816,6 +865,7 @@ og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* nc
     }
     R->nts = nts;
     free(hits); free(Li); free(Lf); free(xb); free(keep); free(T); free(tv);
+    free(trace); free(trace_keep); free(X);
     return R;
 }
 
@@ -1002,7 +1052,7 @@ void og_is_samples(const og_graph *g, const int *T, int a, const og_is_params *p
         }
         int kl;
         fail[i] = (unsigned char)og_decode_nms(g, L, p->K, p->sat, p->alpha_num, p->alpha_shift, 1, xb, &kl,
-                                              NULL, NULL);
+                                              NULL, NULL, NULL);
         double lw = 0.0;
         for (int v = 0; v < g->n; v++)
             if (inT[v]) lw = lw + ((double)nv[v] * A - Bc);
