@@ -92,6 +92,9 @@ def lib():
             L.og_decode_nms.argtypes = [vp, I32P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                         U8P, C.POINTER(C.c_int), I32P, I32P, vp]
             L.og_decode_nms.restype = C.c_int
+            L.og_decode_lnms.argtypes = [vp, I32P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, U8P,
+                                         C.POINTER(C.c_int)]
+            L.og_decode_lnms.restype = C.c_int
             L.og_decode_spa.argtypes = [vp, F32P, C.c_int, C.c_float, C.c_int, U8P,
                                         C.POINTER(C.c_int), I32P]
             L.og_decode_spa.restype = C.c_int
@@ -263,6 +266,16 @@ class Graph:
         # with trace, self.last_trace[k] = x_k for k = 0..K_last
         self.last_trace = xt[: kl.value + 1] if trace else None
         return bool(f), xb, kl.value, ut[: kl.value + 1]
+
+    def decode_lnms(self, Lv, K=20, llr_bits=4, c2v_bits=4, v2c_bits=6, alpha_num=3, alpha_shift=2):
+        """The quantized layered normalized min-sum of the paper's simulations:
+        returns (failed, x, iterations run)."""
+        Lv = np.ascontiguousarray(np.asarray(Lv, dtype=np.int32))
+        x = np.zeros(self.n, dtype=np.uint8)
+        kl = C.c_int()
+        f = lib().og_decode_lnms(self.h, Lv, K, llr_bits, c2v_bits, v2c_bits, alpha_num, alpha_shift, x,
+                                 C.byref(kl))
+        return bool(f), x, kl.value
 
     def decode_spa(self, Lv, K, clip=30.0, wstart=None):
         Lv = np.ascontiguousarray(np.asarray(Lv, dtype=np.float32))

@@ -20,6 +20,9 @@
  *   sum-product decoder                 exact MAP on a cycle-free code
  *   bisection                           linear scan on the tiny code
  *   importance-sampling weights         closed forms (mu = 0, Gaussian moments)
+ *   ordered list over iterations        dense-matrix restatement on the decoder's x_k trace
+ *   layered simulation decoder          hand-computed iterations; QC layer = its rows one by one;
+ *                                       saturation of each width; codeword inputs
  * The decoders themselves are not specified by the paper ("our used version
  * of message passing decoder", Sec. III), so the decoder arithmetic has no
  * paper pin beyond the substitutes above.
@@ -412,6 +415,78 @@ int og_decode_nms(const og_graph *g, const int *L, int K, int sat, int an, int a
     for (int v = 0; v < g->n; v++) fail |= x[v];
     *K_last = kl;
     free(q); free(r); free(x);
+    return fail;
+}
+
+/* The simulation decoder of Sec. III (the FER curves of Fig. 2): quantized
+ * normalized layered min-sum, LLR 4 bits, check-to-variable 4 bits,
+ * variable-to-check 6 bits, 20 iterations.  The paper names the widths and
+ * nothing else; readings:
+ *   - every quantity is a signed integer; a w-bit value saturates to
+ *     +-(2^(w-1) - 1); the channel LLR L_v is saturated to the LLR width;
+ *   - a layer is a row block of the QC base matrix (whose checks touch
+ *     distinct variable nodes), for a general code one check row, in order;
+ *   - the posterior P_v (start: L_v) is kept at the variable-to-check width;
+ *   - one layer: for every edge (c, v) of the layer, from the P_v before the
+ *     layer, q = sat_v2c(P_v - r(c,v)); then for every check of the layer
+ *     r(c,v) = s * sat_c2v((an * m) >> as), m = min over v' != v of |q(c,v')|
+ *     (sat_c2v when c has no other edge), s = product of their signs
+ *     (sgn 0 = +1); then P_v = sat_v2c(q(c,v) + r(c,v));
+ *   - after each full iteration x_v = [P_v < 0], u = unsatisfied checks; stop
+ *     at u = 0 (also before the first iteration) or after K iterations.
+ * Returns 1 if x != 0 at the end; x_out receives x, *K_last the iterations run. */
+static int satw(int x, int w) {
+    const int lim = (1 << (w - 1)) - 1;
+    return x < -lim ? -lim : x > lim ? lim : x;
+}
+int og_decode_lnms(const og_graph *g, const int *L, int K, int llr_bits, int c2v_bits, int v2c_bits, int an,
+                   int as, unsigned char *x_out, int *K_last) {
+    const int E = g->m * g->dcmax;
+    int *r = (int *)calloc((size_t)E, sizeof(int)), *q = (int *)malloc(sizeof(int) * E);
+    int *P = (int *)malloc(sizeof(int) * g->n);
+    unsigned char *x = (unsigned char *)malloc(g->n);
+    for (int v = 0; v < g->n; v++) { P[v] = satw(L[v], llr_bits); x[v] = P[v] < 0; }
+    const int layer = g->Z > 0 ? g->Z : 1;   /* checks per layer */
+    const int nl = g->m / layer;
+    int u = unsat_count(g, x), kl = 0;
+    for (int k = 1; k <= K && u != 0; k++) {
+        for (int l = 0; l < nl; l++) {
+            const int c0 = l * layer, c1 = c0 + layer;
+            for (int c = c0; c < c1; c++)
+                for (int p = 0; p < g->cdeg[c]; p++) {
+                    const int e = c * g->dcmax + p;
+                    q[e] = satw(P[g->cadj[e]] - r[e], v2c_bits);
+                }
+            for (int c = c0; c < c1; c++) {
+                const int d = g->cdeg[c];
+                for (int p = 0; p < d; p++) {
+                    int mn = 1 << 30, sg = 1;
+                    for (int p2 = 0; p2 < d; p2++) {
+                        if (p2 == p) continue;
+                        const int qq = q[c * g->dcmax + p2];
+                        const int mag = qq < 0 ? -qq : qq;
+                        if (mag < mn) mn = mag;
+                        if (qq < 0) sg = -sg;
+                    }
+                    const int mag = d == 1 ? (1 << (c2v_bits - 1)) - 1 : satw((an * mn) >> as, c2v_bits);
+                    r[c * g->dcmax + p] = sg * mag;
+                }
+            }
+            for (int c = c0; c < c1; c++)
+                for (int p = 0; p < g->cdeg[c]; p++) {
+                    const int e = c * g->dcmax + p;
+                    P[g->cadj[e]] = satw(q[e] + r[e], v2c_bits);
+                }
+        }
+        for (int v = 0; v < g->n; v++) x[v] = P[v] < 0;
+        u = unsat_count(g, x);
+        kl = k;
+    }
+    int fail = 0;
+    for (int v = 0; v < g->n; v++) fail |= x[v];
+    if (x_out) memcpy(x_out, x, g->n);
+    *K_last = kl;
+    free(r); free(q); free(P); free(x);
     return fail;
 }
 
