@@ -228,7 +228,11 @@ TSX_API int tune_tile(tsx_code *code, const tsx_enum_params *params, void *strea
  *     device; params[i].kernel = 1 (one codeword per group) and codes whose
  *     min-sum parameters leave the two-codeword kernel's 16-bit bounds, the
  *     float decoder, or a mix of QC and CSR codes or of decoders, fall back to
- *     one decode launch per code (batch_multi_launch() returns 0).
+ *     one decode launch per code (batch_multi_launch() returns 0); a code
+ *     whose two-codeword layout does not fit a CTA's shared memory gets a
+ *     decode launch of its own after the multi-code one (the same kernel
+ *     choice as enumerate_ts() makes for it).  At most 64 codes share the
+ *     multi-code launch (more: one launch per code).
  * Results of run k are read with batch_view(batch, i, ...) after the stream
  * has reached the end of that run; batch_view synchronizes `stream` of the
  * last batch_run.  Errors as for enumerate_ts(). */
