@@ -246,7 +246,8 @@ def run_ours(args):
     info = code.info
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     has_cycles = w["cycle_len"] // 2 > w["max_size"]
-    launches_per_step = 3 + (3 if has_cycles else 0) + 1 + 2
+    # candidates (count, scan, write; again for cycle sets), decode, sieve, compaction (2)
+    launches_per_step = 3 + (3 if has_cycles else 0) + 1 + 1 + 2
 
     def step():
         return tsx.enumerate_ts(code, stream=stream, **params)
@@ -502,7 +503,8 @@ def run_batch(args):
                      "note": "whole step (candidates, decode, sieve) against the decode's ALU bound"},
         "cpu_baseline": None,
         "e2e": e2e,
-        "gpu_launches": (len(codes) * 6 + 1) * args.steps,
+        # per code: candidates (3), sieve, compaction (2); plus the decode launches of the batch
+        "gpu_launches": (len(codes) * 6 + batch.decode_launches) * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

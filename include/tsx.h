@@ -242,6 +242,9 @@ TSX_API int batch_create(tsx_code *const *codes, const tsx_enum_params *params, 
 TSX_API int batch_run(tsx_batch *batch, void *stream);
 TSX_API int batch_size(const tsx_batch *batch);
 TSX_API int batch_multi_launch(const tsx_batch *batch);
+/* Decode launches of one batch_run(): 1 + the codes with a launch of their
+ * own when the multi-code launch is used, else one per code. */
+TSX_API int batch_decode_launches(const tsx_batch *batch);
 /* Results of code i of the last run (same contents as ts_list_view()). */
 TSX_API int batch_view(tsx_batch *batch, int32_t i, tsx_ts_view *view);
 /* Sums of the device counters of all codes of the last run. */

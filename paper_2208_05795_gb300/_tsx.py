@@ -157,6 +157,8 @@ def lib():
             L.batch_size.restype = C.c_int
             L.batch_multi_launch.argtypes = [vp]
             L.batch_multi_launch.restype = C.c_int
+            L.batch_decode_launches.argtypes = [vp]
+            L.batch_decode_launches.restype = C.c_int
             L.batch_view.argtypes = [vp, C.c_int32, C.POINTER(TsView)]
             L.batch_view.restype = C.c_int
             L.batch_stats.argtypes = [vp, C.POINTER(EnumStats)]
@@ -373,6 +375,10 @@ class Batch:
     @property
     def multi_launch(self) -> bool:
         return bool(lib().batch_multi_launch(self.h))
+
+    @property
+    def decode_launches(self) -> int:
+        return int(lib().batch_decode_launches(self.h))
 
     def __del__(self):
         if getattr(self, "h", None):

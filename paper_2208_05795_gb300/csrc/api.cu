@@ -813,6 +813,14 @@ extern "C" int batch_size(const tsx_batch *B) { return B ? (int)B->lists.size() 
 
 extern "C" int batch_multi_launch(const tsx_batch *B) { return B && B->multi ? 1 : 0; }
 
+extern "C" int batch_decode_launches(const tsx_batch *B) {
+    if (!B) return 0;
+    if (!B->multi) return (int)B->lists.size();
+    int n = 1;
+    for (bool own : B->own) n += own ? 1 : 0;
+    return n;
+}
+
 extern "C" int batch_view(tsx_batch *B, int32_t i, tsx_ts_view *view) {
     if (!B || i < 0 || i >= (int)B->lists.size()) return TSX_EINVAL;
     return ts_list_view(B->lists[i], view);
