@@ -413,9 +413,10 @@ TSX_API void server_destroy(tsx_server *server);
  *   n_cand * (28 + 4 * ceil(n / 32)) + ~2 KB > TSX_NOALLOC_SCRATCH_BYTES,
  * TSX_EINVAL for a malformed candidate set (checked on the device; this
  * check waits for the stream), a misaligned pointer or a code loaded on
- * another device.  The decode itself is enqueued on `stream` and not waited
- * for.  The first call on each device looks up the array's device address
- * (make that first call before any stream capture).  Every call uses the
+ * another device.  The call waits for `stream` once, after the candidate
+ * check; the decode itself is enqueued on `stream` and not waited for.  The
+ * first call on each device looks up the array's device address (make that
+ * first call before any stream capture).  Every call uses the
  * same array and finds the previous call's contents in it; the counters it
  * relies on are reset at the start of each call, so calls that overlap on
  * the GPU (on different streams or threads) race and must not be issued. */

@@ -126,6 +126,9 @@ def lib():
             L.og_normals4.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, F32P]
             L.og_is_samples.argtypes = [C.c_void_p, I32P, C.c_int, C.POINTER(_IsParams), C.c_uint64, C.c_int,
                                         U8P, F64P]
+            L.og_is_quant.argtypes = [C.c_float, C.c_float, C.c_int]
+            L.og_is_quant.restype = C.c_int
+            L.og_is_channel.argtypes = [C.c_void_p, I32P, C.c_int, C.POINTER(_IsParams), C.c_uint64, I32P, F32P]
             _lib = L
     return _lib
 
@@ -153,6 +156,12 @@ def normals4(job: int, sample: int, quad: int) -> np.ndarray:
     g = np.zeros(4, dtype=np.float32)
     lib().og_normals4(int(job), int(sample), int(quad), g)
     return g
+
+
+def is_quant(y: float, cq: float, sat: int) -> int:
+    """The importance-sampling channel quantizer: round-half-away(y * cq) in
+    single precision, saturated to [-sat, sat]."""
+    return int(lib().og_is_quant(float(y), float(cq), int(sat)))
 
 
 def tanhf(x: float) -> float:
@@ -332,6 +341,16 @@ class Graph:
         logw = np.zeros(n, dtype=np.float64)
         lib().og_is_samples(self.h, Ta, Ta.size, C.byref(p), int(s0), int(n), fail, logw)
         return fail, logw
+
+    def is_channel(self, T, *, ebn0_db, rate=None, mu=1.0, job=0, sample=0, sat=511):
+        """The quantized channel LLRs and the drawn noise (before the shift) of one sample."""
+        Ta = np.ascontiguousarray(np.sort(np.asarray(list(T), dtype=np.int32)))
+        r = (1.0 - self.m / self.n) if rate is None else rate
+        p = _IsParams(float(ebn0_db), float(r), float(mu), int(job), 20, sat, 3, 2)
+        L = np.zeros(self.n, dtype=np.int32)
+        nv = np.zeros(self.n, dtype=np.float32)
+        lib().og_is_channel(self.h, Ta, Ta.size, C.byref(p), int(sample), L, nv)
+        return L, nv
 
     # --- the whole method -----------------------------------------------
     def enumerate(self, cands=None, *, decoder="nms", K=20, base_llr=16, sat=511, alpha_num=3,

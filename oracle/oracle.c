@@ -1099,6 +1099,42 @@ static void og_is_consts(const og_is_params *p, float *sigf, float *muf, float *
     *Bc = p->mu * p->mu / (2.0 * s2);
 }
 
+/* The channel quantizer: 8 * (2 y / sigma^2) = y * cq with cq = 16 / sigma^2
+ * in single precision, rounded half away from zero (roundf), saturated to
+ * [-sat, sat]. */
+int og_is_quant(float y, float cq, int sat) {
+    float lq = roundf(y * cq);
+    return lq > (float)sat ? sat : lq < -(float)sat ? -sat : (int)lq;
+}
+
+/* The channel of sample s: fixed-point LLRs L[v] and the drawn noise n[v]
+ * (before the shift toward T) of every variable node; inT marks T. */
+static void og_is_channel_mask(const og_graph *g, const unsigned char *inT, const og_is_params *p, uint64_t s,
+                               int *L, float *nv) {
+    float sigf, muf, cq;
+    double A, Bc;
+    og_is_consts(p, &sigf, &muf, &cq, &A, &Bc);
+    for (int q = 0; 4 * q < g->n; q++) {
+        float gq[4];
+        og_normals4(p->job, s, (uint32_t)q, gq);
+        for (int j = 0; j < 4 && 4 * q + j < g->n; j++) {
+            int v = 4 * q + j;
+            float n = sigf * gq[j];
+            float y = 1.0f + n;
+            if (inT[v]) y = y - muf;
+            L[v] = og_is_quant(y, cq, p->sat);
+            nv[v] = n;
+        }
+    }
+}
+
+void og_is_channel(const og_graph *g, const int *T, int a, const og_is_params *p, uint64_t s, int *L, float *nv) {
+    unsigned char *inT = (unsigned char *)calloc(g->n, 1);
+    for (int t = 0; t < a; t++) inT[T[t]] = 1;
+    og_is_channel_mask(g, inT, p, s, L, nv);
+    free(inT);
+}
+
 /* Samples [s0, s0 + ns): fail flags and log-weights. */
 void og_is_samples(const og_graph *g, const int *T, int a, const og_is_params *p, uint64_t s0, int ns,
                    unsigned char *fail, double *logw) {
@@ -1111,20 +1147,7 @@ void og_is_samples(const og_graph *g, const int *T, int a, const og_is_params *p
     for (int t = 0; t < a; t++) inT[T[t]] = 1;
     for (int i = 0; i < ns; i++) {
         uint64_t s = s0 + (uint64_t)i;
-        for (int q = 0; 4 * q < g->n; q++) {
-            float gq[4];
-            og_normals4(p->job, s, (uint32_t)q, gq);
-            for (int j = 0; j < 4 && 4 * q + j < g->n; j++) {
-                int v = 4 * q + j;
-                float n = sigf * gq[j];
-                float y = 1.0f + n;
-                if (inT[v]) y = y - muf;
-                float lq = roundf(y * cq);
-                int li = lq > (float)p->sat ? p->sat : lq < -(float)p->sat ? -p->sat : (int)lq;
-                L[v] = li;
-                nv[v] = n;
-            }
-        }
+        og_is_channel_mask(g, inT, p, s, L, nv);
         int kl;
         fail[i] = (unsigned char)og_decode_nms(g, L, p->K, p->sat, p->alpha_num, p->alpha_shift, 1, xb, &kl,
                                               NULL, NULL, NULL);

@@ -729,6 +729,15 @@ __device__ unsigned long long key_hash(const uint16_t *key, int a, int lane) {
     return h + mix64(0xabcdef0000000000ull + (unsigned long long)a);
 }
 
+// Space reserved at pool offset off for a key of a nodes that another
+// insert of the same key made unnecessary: taken back if nothing was
+// reserved after it, else counted as leaked.
+__device__ __forceinline__ void pool_giveback(const EnumBuffers &b, long long off, int a) {
+    const unsigned long long len = (unsigned long long)(kPoolHdr + a);
+    const unsigned long long top = (unsigned long long)(off - 1);  // pool_top before the reservation
+    if (atomicCAS(&b.ctr->pool_top, top + len, top) != top + len) atomicAdd(&b.ctr->pool_leaked, len);
+}
+
 // Insert / find the key; returns the table slot, -1 on a full table, -2 on
 // a pool overflow.  Warp-collective.  The header's flags word ends as the OR
 // of the flags of every insert of the key (independent of their order).
@@ -777,13 +786,19 @@ __device__ long long ts_insert(const EnumBuffers &b, const uint16_t *key, int a,
                 for (int i = lane; i < a && eq; i += 32) eq = __ldcg(&b.pool[off + kPoolHdr + i]) == (int)key[i];
             if (__all_sync(0xffffffffu, eq)) {
                 // the sieve bits of a set are the union over every candidate that reached it
-                if (lane == 0) atomicOr(&b.pool[off + 3], flags);
+                if (lane == 0) {
+                    atomicOr(&b.pool[off + 3], flags);
+                    if (my_off >= 0) pool_giveback(b, my_off, a);
+                }
                 return (long long)slot;
             }
         }
         slot = (slot + 1) & b.cap_mask;
     }
-    if (lane == 0) atomicOr(&b.ctr->err, kErrTableFull);
+    if (lane == 0) {
+        atomicOr(&b.ctr->err, kErrTableFull);
+        if (my_off >= 0) pool_giveback(b, my_off, a);
+    }
     return -1;
 }
 

@@ -1,11 +1,12 @@
 // noalloc.cu -- decode_thresholds_noalloc(): the impulse-decoding kernel run
 // on caller-given candidate sets with all of its working memory in one
 // fixed device array, for callers that cannot allocate device memory (a
-// host thread that must not take the driver's allocation locks or
-// synchronize, code running under another framework's memory manager that
-// forbids outside cudaMalloc, or a process that has reserved the whole
-// device).  The paper has no counterpart; the decoding is the same kernel
-// enumerate_ts() uses.
+// host thread that must not take the driver's allocation locks, code running
+// under another framework's memory manager that forbids outside cudaMalloc,
+// or a process that has reserved the whole device).  The call does wait for
+// its stream once, for the device-side check of the candidate sets.  The
+// paper has no counterpart; the decoding is the same kernel enumerate_ts()
+// uses.
 #include <mutex>
 
 #include "kernels.cuh"
@@ -84,6 +85,9 @@ extern "C" int decode_thresholds_noalloc(const tsx_code *code, const tsx_enum_pa
     if (dev != code_device(code)) return TSX_EINVAL;
     const DevCode &g = *code_dev(code);
     const int nw = (g.n + 31) / 32;
+    // 28 + 4 nw bytes per candidate: refuse a count beyond the array before
+    // any size arithmetic can wrap
+    if ((uint64_t)n_cand > (uint64_t)TSX_NOALLOC_SCRATCH_BYTES / (28u + 4u * (uint64_t)nw)) return TSX_ENOMEM;
     // carve: counters | bad flag | checked sets | thr_f | slot | flags | x*
     const size_t off_bad = al256(sizeof(Counters));
     const size_t off_cands = al256(off_bad + sizeof(unsigned));

@@ -63,6 +63,8 @@ struct Counters {
     unsigned long long acyclic;
     unsigned long long next_sieve;  // work queue of the sieve kernel
     unsigned long long n_fail;      // importance sampling: failing samples
+    unsigned long long pool_leaked; // key-pool words reserved by an insert that lost to an equal key
+                                    // and could not be given back
     unsigned int n_ts;
     unsigned int err;               // bit flags, see kErr*
 };

@@ -243,3 +243,52 @@ def test_series_tanh_atanh_error_bounds():
         assert abs(got - want) <= 4 * np.spacing(np.float32(abs(want))) + 1e-45, p
     assert oracle.tanhf(0.0) == 0.0 and oracle.atanhf(0.0) == 0.0
     assert oracle.tanhf(20.0) == 1.0
+
+
+def _xstar_cases(code, K, n_trials, seed):
+    """Decodes of noisy channel values with the x_k trace; u_k recomputed from
+    H independently of the decoder."""
+    g = oracle.Graph(code)
+    H = g.dense().astype(np.int64)
+    ws = max(1, g.girth() // 2)
+    rng = np.random.default_rng(seed)
+    for _ in range(n_trials):
+        L = np.round(rng.normal(16, 14, g.n)).astype(np.int32)
+        f, xb, kl, u = g.decode_nms(L, K=K, trace=True)
+        xt = g.last_trace
+        assert np.array_equal((H @ xt.T.astype(np.int64) % 2).sum(0), u)
+        yield ws, kl, u, xt, xb
+
+
+@pytest.mark.parametrize("name", ["qc96", "qc2640"])
+def test_best_pattern_first_minimum_in_window(name):
+    # Sec. III: the potential trapping set is S(min_iter w_H(H x_iter)) with the
+    # list starting at x_floor(girth/2).  Reading: x* = x_k at the FIRST k in
+    # [max(1, floor(g/2)), K_last] with minimal u_k; x_{K_last} when K_last is
+    # below the window.  Each case below is one that a wrong rule gets wrong:
+    # taking the last minimum (a tie with differing patterns), a window that
+    # starts one late (the unique minimum sits at floor(g/2)) or one early (a
+    # smaller u_k just before the window).
+    w = synth.workload(name)
+    seen = {"tie": 0, "at_start": 0, "before_start": 0, "short": 0}
+    for ws, kl, u, xt, xb in _xstar_cases(w["code"], 20 if name == "qc96" else 30, 3000 if name == "qc96" else 150,
+                                          seed=5):
+        if kl < ws:
+            assert np.array_equal(xb, xt[kl])
+            seen["short"] += 1
+            continue
+        win = u[ws:kl + 1]
+        ks = [ws + i for i in np.flatnonzero(win == win.min())]
+        assert np.array_equal(xb, xt[ks[0]])
+        if len(ks) >= 2 and not np.array_equal(xt[ks[0]], xt[ks[-1]]):
+            seen["tie"] += 1
+        if ks == [ws] and kl > ws:
+            late = ws + 1 + int(np.argmin(u[ws + 1:kl + 1]))
+            if not np.array_equal(xt[ws], xt[late]):
+                seen["at_start"] += 1
+        if ws >= 2 and u[ws - 1] < win.min() and not np.array_equal(xt[ws - 1], xt[ks[0]]):
+            seen["before_start"] += 1
+    if name == "qc96":
+        assert all(c > 0 for c in seen.values()), seen
+    else:
+        assert seen["tie"] > 0, seen

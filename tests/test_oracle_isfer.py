@@ -82,3 +82,43 @@ def test_unbiased_against_plain_monte_carlo():
     se = math.sqrt(p0 * (1 - p0) / N + w.var() / N)
     assert p0 > 0.01
     assert abs(p1 - p0) < 5 * se, (p0, p1, se)
+
+
+def test_quantizer_rounds_half_away_and_saturates():
+    # 8 * LLR rounded half away from zero (round-to-even would give 2, -2, 0)
+    for y, cq, sat, want in ((2.5, 1.0, 511, 3), (-2.5, 1.0, 511, -3), (0.5, 1.0, 511, 1), (-0.5, 1.0, 511, -1),
+                             (1.5, 1.0, 511, 2), (0.4999999701976776, 1.0, 511, 0), (0.75, 2.0, 511, 2),
+                             (600.0, 1.0, 511, 511), (-600.0, 1.0, 511, -511), (3.0, 2.0, 5, 5), (-3.0, 2.0, 5, -5)):
+        assert oracle.is_quant(y, cq, sat) == want, (y, cq, sat)
+
+
+@pytest.mark.parametrize("ebn0,mu,sat", [(4.0, 1.0, 511), (0.0, 0.7, 20)])
+def test_channel_llr_from_the_definition(ebn0, mu, sat):
+    # channel LLR 2 y / sigma^2 in units of 1/8 (x 16 / sigma^2), y = 1 + n - mu [v in T],
+    # sigma^2 = 1 / (2 R Eb/N0), rounded half away from zero and saturated to +-sat;
+    # recomputed here from the drawn normals, then decoded to the same fail flags
+    g, T = _tiny()
+    R = 1.0 - g.m / g.n
+    s2 = 1.0 / (2.0 * R * 10.0 ** (ebn0 / 10.0))
+    sig = np.float32(math.sqrt(s2))
+    cq = np.float32(16.0 / s2)
+    inT = np.zeros(g.n, bool)
+    inT[list(T)] = True
+    job = 21
+    n_sat = 0
+    for s in range(40):
+        gn = np.concatenate([oracle.normals4(job, s, q) for q in range((g.n + 3) // 4)])[:g.n].astype(np.float32)
+        n = (sig * gn).astype(np.float32)
+        y = (np.float32(1.0) + n).astype(np.float32)
+        y = np.where(inT, (y - np.float32(mu)).astype(np.float32), y)
+        prod = (y * cq).astype(np.float32).astype(np.float64)
+        want = np.clip(np.sign(prod) * np.floor(np.abs(prod) + 0.5), -sat, sat).astype(np.int32)
+        L, nv = g.is_channel(T, ebn0_db=ebn0, mu=mu, job=job, sample=s, sat=sat)
+        assert np.array_equal(nv, n)
+        assert np.array_equal(L, want), s
+        n_sat += int((np.abs(want) == sat).sum())
+        fail, _ = g.is_samples(T, ebn0_db=ebn0, mu=mu, job=job, s0=s, n=1, sat=sat)
+        f, *_ = g.decode_nms(want, K=20, sat=sat, wstart=1)
+        assert bool(fail[0]) == f
+    if sat < 100:
+        assert n_sat > 0

@@ -73,6 +73,10 @@ def test_noalloc_limits_and_bad_input():
     st = tsx.decode_thresholds_noalloc(code, c.data_ptr(), 10 ** 9, out.data_ptr(), None, out.data_ptr(),
                                        out.data_ptr(), check=False, **p)
     assert st == TSX_ENOMEM
+    # a count whose byte size would wrap a 64-bit size: refused the same way
+    st = tsx.decode_thresholds_noalloc(code, c.data_ptr(), 2 ** 62, out.data_ptr(), None, out.data_ptr(),
+                                       out.data_ptr(), check=False, **p)
+    assert st == TSX_ENOMEM
     # a node index outside the code is caught by the device-side check
     st, *_ = _noalloc(code, np.array([[0, 96, -1, -1]], dtype=np.int32), p, check=False)
     assert st == TSX_EINVAL
