@@ -19,11 +19,23 @@ one multi-code persistent decode launch, the whole step captured once in a
 CUDA graph and replayed; the same codes run one enumerate_ts() at a time are
 timed beside it ("serial").
 
+At one GPU the default run also measures, after the headline, the other
+workloads of the library with a few steps each and reports them as extra
+keys of the one JSON line: the batch of 32 codes (tuned tiles, against one
+enumerate_ts() per code), the serving stream (p50/p99 against the plain
+one-job-at-a-time method, results compared), and the importance-sampling
+job (--no-extras skips them).
+
+Rooflines: the decoders are bound by integer issue and shared-memory
+bandwidth; measure_peaks() measures both per SM clock on the device, and the
+peak is taken at the SM clock sampled during the timed region.  The
+two-codeword kernels do two edge updates per 16-bit-pair lane operation.
+
 Multi-GPU (torchrun): every rank enumerates its own code of the same shape
 (rank r uses seed offset r: independent problems, weak scaling); no
 collective on the data path, a barrier and max-over-ranks time only.
---impl reference times the CPU oracle (single thread) on a bounded sample
-of the same workload each step.
+--impl reference times the CPU oracle, as it stands, on a bounded sample of
+the same workload each step, over all host cores (one process per core).
 """
 from __future__ import annotations
 
@@ -49,16 +61,44 @@ from paper_2208_05795_gb300.shard import reduce_time_and_work  # noqa: E402
 # x3, >>2, sign apply, the add of the variable-node sum, the subtract of
 # P - r and the two-sided clamp (counted as one)
 ALG_OPS_PER_EDGE = 12
-# INT32 lanes per SM that execute IADD3/LOP3 each clock (Blackwell SM: 4
-# partitions x 32 lanes); with 152 SMs at the 2070 MHz maximum SM clock.
-INT_LANES_PER_SM = 128
-N_SMS = 152
+# shared-memory bytes an edge update needs at minimum: write and read one
+# 16-bit check-to-variable message (posterior and variable-to-check message
+# are recomputable)
+ALG_SMEM_BYTES_PER_EDGE = 4
+# DRAM bytes (read + write) an ncu capture measured for the PEG decode launch over its first
+# 40,000 candidates; None until captured for the kernel as it stands
+PAIR_KERNEL_DRAM_BYTES_40K = None
 SM_MAX_MHZ = 2070.0
 try:  # the maximum SM clock measured on this machine, when the measurement file is present
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
         SM_MAX_MHZ = float(json.load(_f).get("sm_max_mhz", SM_MAX_MHZ))
 except (OSError, ValueError):
     pass
+
+
+def alu_roofline(eu_per_launch, ms_launch, pk, sm_mhz, packed=True, traffic=None, note=""):
+    """Roofline of a min-sum decode launch in edge updates per second:
+    min(integer lane-ops/s x values per lane-op / 12, shared-memory B/s / 4),
+    from the measured per-clock rates at the sampled SM clock."""
+    mhz = sm_mhz or SM_MAX_MHZ
+    clk = mhz * 1e6 * pk["num_sms"]
+    per_op = 2 if packed else 1
+    lane = pk["u16x2_ops_per_clk_sm"] if packed else pk["int32_ops_per_clk_sm"]
+    int_bound = lane * clk * per_op / ALG_OPS_PER_EDGE
+    smem_bound = pk["smem_bytes_per_clk_sm"] * clk / ALG_SMEM_BYTES_PER_EDGE
+    peak = min(int_bound, smem_bound)
+    achieved = eu_per_launch / (ms_launch / 1e3)
+    unpacked = pk["int32_ops_per_clk_sm"] * clk / ALG_OPS_PER_EDGE
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "edge-updates/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "terms": {"int_bound": int_bound, "smem_bound": smem_bound, "sm_mhz": mhz, "num_sms": pk["num_sms"],
+                      "int32_ops_per_clk_sm": pk["int32_ops_per_clk_sm"],
+                      "u16x2_ops_per_clk_sm": pk["u16x2_ops_per_clk_sm"],
+                      "smem_bytes_per_clk_sm": pk["smem_bytes_per_clk_sm"], "ops_per_edge": ALG_OPS_PER_EDGE,
+                      "values_per_lane_op": per_op, "smem_bytes_per_edge": ALG_SMEM_BYTES_PER_EDGE,
+                      "achieved_int_ops_per_s": ALG_OPS_PER_EDGE * achieved,
+                      "frac_of_unpacked_int32": achieved / unpacked},
+            "note": note or "peaks measured by measure_peaks() per SM clock, at the sampled median SM clock"}
 
 
 def parse():
@@ -83,6 +123,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cand-limit", type=int, default=-1,
                     help="decode only the first N canonical candidates (profiling a bounded case)")
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only (no extra workloads)")
+    ap.add_argument("--procs", type=int, default=0, help="oracle processes (0 = every host core)")
     return ap.parse_args()
 
 
@@ -161,29 +203,80 @@ class Clocks:
                 "reasons": reasons, "samples": len(busy)}
 
 
-def cpu_baseline(w, decoder, seconds, rng_seed=0):
-    """The oracle (single thread, as it stands) on a bounded random sample of
-    the workload's canonical candidates; edge-updates/s."""
+def _oracle_chunk(job):
+    """One worker's share of an oracle timing: (iterations, seconds)."""
+    import oracle
+    code, rows, p, od = job
+    g = oracle.Graph(code)
+    t0 = time.perf_counter()
+    res = g.enumerate(rows, decoder=od, **p)
+    return int(res.iters.sum()), time.perf_counter() - t0
+
+
+class OraclePool:
+    """The oracle on every host core: one spawned process per core (spawned,
+    so that no worker inherits a CUDA context)."""
+
+    def __init__(self, procs=0):
+        import multiprocessing as mp
+        self.procs = procs or os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+
+    def run(self, code, rows, p, od):
+        """Wall seconds and summed iterations of enumerating `rows`, split over
+        the processes."""
+        chunks = [c for c in np.array_split(rows, self.procs * 4) if len(c)]
+        t0 = time.perf_counter()
+        out = self.pool.map(_oracle_chunk, [(code, c, p, od) for c in chunks], chunksize=1)
+        return time.perf_counter() - t0, sum(o[0] for o in out)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def _oracle_args(w, decoder):
+    p = params_of(w, decoder)
+    p.pop("decoder")
+    if decoder == "nms8":
+        p["sat"] = 127
+    return p, ("spa" if decoder == "spa" else "nms")
+
+
+def cpu_baseline(w, decoder, seconds, rng_seed=0, procs=0):
+    """The oracle, as it stands, on bounded random samples of the workload's
+    canonical candidates: single-threaded, then over every host core;
+    edge-updates/s."""
     import oracle
     g = oracle.Graph(w["code"])
     cands = g.candidates(w["max_size"], w["cycle_len"])
     rng = np.random.default_rng(rng_seed)
-    p = params_of(w, decoder)
-    p.pop("decoder")
-    od = "spa" if decoder == "spa" else "nms"
-    extra = dict(sat=127) if decoder == "nms8" else {}
+    p, od = _oracle_args(w, decoder)
     n, it, el, ncand = 4, 0, 0.0, 0
-    while el < seconds:
+    while el < seconds / 2:
         pick = rng.choice(len(cands), min(n, len(cands)), replace=False)
         t0 = time.perf_counter()
-        res = g.enumerate(cands[np.sort(pick)], decoder=od, **p, **extra)
+        res = g.enumerate(cands[np.sort(pick)], decoder=od, **p)
         el += time.perf_counter() - t0
         it += int(res.iters.sum())
         ncand += len(pick)
         n = min(len(cands), n * 2)
-    return {"value": it * g.E / el, "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{ncand} random canonical candidates of {len(cands)} (seeded), "
-                      f"{el:.1f} s single-threaded"}, ncand / el
+    single = {"value": it * g.E / el, "cores": 1,
+              "sample": f"{ncand} random canonical candidates of {len(cands)} (seeded), {el:.1f} s"}
+    rate1 = ncand / el
+    pool = OraclePool(procs)
+    try:
+        pool.run(w["code"], cands[:pool.procs], p, od)  # start the workers
+        want = int(rate1 * pool.procs * seconds / 2) + pool.procs
+        pick = np.sort(rng.choice(len(cands), min(want, len(cands)), replace=False))
+        wall, it_all = pool.run(w["code"], cands[pick], p, od)
+    finally:
+        pool.close()
+    return {"value": it_all * g.E / wall, "unit": "edge-updates/s", "cores": pool.procs, "kind": "oracle",
+            "nproc": os.cpu_count(),
+            "sample": f"{len(pick)} random canonical candidates of {len(cands)} (seeded), {wall:.1f} s wall over "
+                      f"{pool.procs} processes",
+            "single_thread": single}, rate1
 
 
 def run_reference(args):
@@ -195,20 +288,23 @@ def run_reference(args):
     import oracle
     g = oracle.Graph(w["code"])
     cands = g.candidates(w["max_size"], w["cycle_len"])
-    p = params_of(w, args.decoder)
-    p.pop("decoder")
-    od = "spa" if args.decoder == "spa" else "nms"
+    p, od = _oracle_args(w, args.decoder)
     rng = np.random.default_rng(1)
-    per_step = max(8, int(len(cands) / 2000))
-    per_step = min(per_step, 64)
-    for s in range(args.warmup + args.steps):
-        pick = np.sort(rng.choice(len(cands), per_step, replace=False))
-        t0 = time.perf_counter()
-        res = g.enumerate(cands[pick], decoder=od, **p)
-        dt = time.perf_counter() - t0
-        if s >= args.warmup:
-            times.append(dt)
-            eus.append(int(res.iters.sum()) * g.E)
+    pool = OraclePool(args.procs)
+    try:
+        # per step about 3 s of the pool's time, from a calibration sample
+        pool.run(w["code"], cands[:pool.procs], p, od)  # start the workers
+        cal = np.sort(rng.choice(len(cands), min(len(cands), 16 * pool.procs), replace=False))
+        wall, _ = pool.run(w["code"], cands[cal], p, od)
+        per_step = int(min(len(cands), max(pool.procs, len(cal) * 3.0 / max(wall, 1e-3))))
+        for s in range(args.warmup + args.steps):
+            pick = np.sort(rng.choice(len(cands), per_step, replace=False))
+            dt, it = pool.run(w["code"], cands[pick], p, od)
+            if s >= args.warmup:
+                times.append(dt)
+                eus.append(it * g.E)
+    finally:
+        pool.close()
     value = sum(eus) / sum(times)
     line = {"impl": "reference", "metric": "impulse-decode edge-updates/s", "value": value,
             "unit": "edge-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -216,8 +312,10 @@ def run_reference(args):
             "vs_baseline": None, "dtype": "f32" if args.decoder == "spa" else "int16", "data": "synthetic",
             "config": {"workload": args.workload, "decoder": args.decoder,
                        "sample_per_step": per_step, "n_cand": int(len(cands))},
-            "cpu_baseline": {"value": value, "unit": "edge-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{per_step} random canonical candidates per step"},
+            "cpu_baseline": {"value": value, "unit": "edge-updates/s", "cores": pool.procs, "kind": "oracle",
+                             "nproc": os.cpu_count(),
+                             "sample": f"{per_step} random canonical candidates per step over {pool.procs} "
+                                       f"processes"},
             "e2e": {"value": value, "unit": "edge-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -235,6 +333,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     tsx_build.build()
+    pk = tsx.measure_peaks()
     w = workload_for(args.workload, rank)
     params = params_of(w, args.decoder)
     if args.decoder == "nms8":
@@ -313,19 +412,21 @@ def run_ours(args):
             dist.barrier()
             dist.destroy_process_group()
         return
-    peak = INT_LANES_PER_SM * N_SMS * SM_MAX_MHZ * 1e6 / 1e12  # Tops/s
     avg_dec_ms = sum(ms_dec) / len(ms_dec)
-    # DRAM bytes (read + write) of one decode launch: an ncu capture of this kernel on the PEG
-    # workload's first 40,000 candidates read 725,504 B and wrote none (candidate sets in, records
-    # out, both proportional to the candidates), scaled to the launch's candidates
-    traffic, traffic_note = None, "not captured for this workload"
-    if args.workload == "peg1008" and args.decoder == "nms16":
-        traffic = 725504.0 / 40000 * float(s["n_cand"])
-        traffic_note = "scaled by candidates from an ncu capture of the first 40,000 (725,504 B)"
+    # DRAM bytes (read + write) of one decode launch, from an ncu capture of this kernel on the PEG
+    # workload's first 40,000 candidates (profiles/pair_kernel_peg1008_40k.md), scaled to the launch's
+    # candidates (candidate sets in, records out: both proportional to the candidates)
+    traffic = None
+    if args.workload == "peg1008" and args.decoder == "nms16" and PAIR_KERNEL_DRAM_BYTES_40K:
+        traffic = PAIR_KERNEL_DRAM_BYTES_40K / 40000 * float(s["n_cand"])
 
     eu_per_step = eu / args.steps
-    achieved = ALG_OPS_PER_EDGE * eu_per_step / (avg_dec_ms / 1e3) / 1e12
-    cpu = cpu_baseline(w, args.decoder, args.cpu_seconds)[0] if args.cpu_seconds > 0 else None
+    roof = (alu_roofline(eu_per_step, avg_dec_ms, pk, clocks.get("sm_mhz"), packed=args.decoder != "spa",
+                         traffic=traffic) if args.decoder != "spa" else None)
+    cpu = cpu_baseline(w, args.decoder, args.cpu_seconds, procs=args.procs)[0] if args.cpu_seconds > 0 else None
+    extras = None
+    if world == 1 and not args.no_extras:
+        extras = run_extras(args, tsx, pk)
     line = {
         "metric": "impulse-decode edge-updates/s",
         "value": value,
@@ -349,15 +450,15 @@ def run_ours(args):
         "n_ts": nts,
         "ms_decode_kernel": avg_dec_ms,
         "ms_candidates": sum(ms_cand) / len(ms_cand),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
-                     "note": f"{ALG_OPS_PER_EDGE} int ops per edge update; peak = {INT_LANES_PER_SM} lanes x "
-                             f"{N_SMS} SMs x {SM_MAX_MHZ:.0f} MHz"},
+        "roofline": roof,
+        "measured_peaks": pk,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if extras:
+        line["extra"] = extras
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -367,7 +468,7 @@ def run_ours(args):
 BATCH = dict(K=20, base_llr=16, amp_steps=10, max_size=2, cycle_len=0)
 
 
-def run_batch(args):
+def run_batch(args, pk=None):
     import torch
     import paper_2208_05795_gb300 as tsx
     from paper_2208_05795_gb300 import build as tsx_build
@@ -471,10 +572,10 @@ def run_batch(args):
         if dist:
             dist.barrier()
             dist.destroy_process_group()
-        return
-    peak = INT_LANES_PER_SM * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
+        return None
+    if pk is None:
+        pk = tsx.measure_peaks()
     ms_step = total_ms / args.steps
-    achieved = ALG_OPS_PER_EDGE * float(s["edge_updates"]) / (ms_step / 1e3) / 1e12
     line = {
         "metric": "impulse-decode edge-updates/s",
         "value": value,
@@ -498,19 +599,18 @@ def run_batch(args):
         "n_ts": int(nts),
         "serial_ms_per_step": statistics.median(serial_ms),
         "batch_speedup_vs_serial": statistics.median(serial_ms) / ms_step,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "note": "whole step (candidates, decode, sieve) against the decode's ALU bound"},
+        "roofline": alu_roofline(float(s["edge_updates"]), ms_step, pk, clocks.get("sm_mhz"),
+                                 note="whole step (candidates, decode, sieve) against the decoders' bound"),
         "cpu_baseline": None,
         "e2e": e2e,
         # per code: candidates (3), sieve, compaction (2); plus the decode launches of the batch
         "gpu_launches": (len(codes) * 6 + batch.decode_launches) * args.steps,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    return line
 
 
 SERVE_ENUM = dict(K=20, base_llr=16, amp_steps=10, max_size=2, cycle_len=0)
@@ -544,7 +644,7 @@ def run_serve(args):
     rank, world, local = rank_world()
     torch.cuda.set_device(local)
     if world > 1 and rank != 0:
-        return  # the serving stream runs on one GPU: replicas only
+        return None  # the serving stream runs on one GPU: replicas only
     tsx_build.build()
     codes, jobs = serve_jobs(args.jobs)
     handles = [tsx.load_code(c) for c in codes]
@@ -638,7 +738,7 @@ def run_serve(args):
                              "chunk sizes (candidate bound taken as the canonical count: a lower bound)",
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def served_launches(jobs, results, chunk_candidates=16384, chunk_samples=32768):
@@ -667,7 +767,7 @@ def isfer_setup(tsx, stream=None):
     return code, h, v["keys"][int(np.argmin(thr))]
 
 
-def run_isfer(args):
+def run_isfer(args, pk=None):
     import torch
     import paper_2208_05795_gb300 as tsx
     from paper_2208_05795_gb300 import build as tsx_build
@@ -711,10 +811,10 @@ def run_isfer(args):
         if dist:
             dist.barrier()
             dist.destroy_process_group()
-        return
-    peak = INT_LANES_PER_SM * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = ALG_OPS_PER_EDGE * (eu / args.steps if not dist else eu / world / args.steps) / (
-        sum(ms) / len(ms) / 1e3) / 1e12
+        return None
+    if pk is None:
+        pk = tsx.measure_peaks()
+    eu_launch = eu / args.steps if not dist else eu / world / args.steps
     line = {
         "metric": "importance-sampling samples/s",
         "value": samples / (total_ms / 1e3),
@@ -733,35 +833,69 @@ def run_isfer(args):
                    "parallelism": f"replicas{world}", "l2": "flushed before each step (256 MB write)"},
         "edge_updates_per_s": eu / (total_ms / 1e3),
         "fer_mean": float(np.mean(fer)), "fails_per_step": nf / args.steps,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
-                     "traffic": None, "note": "12 int ops per edge update of the decodes; the noise generation "
-                                              "is extra work not counted"},
+        "roofline": alu_roofline(eu_launch, sum(ms) / len(ms), pk, clocks.get("sm_mhz"),
+                                 note="edge updates of the decodes against the decoders' bound; the noise "
+                                      "generation is extra work not counted"),
         "cpu_baseline": None,
         "e2e": {"value": args.samples / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": 4 * len(ts),
                 "d2h_bytes_per_step": 96},
         "gpu_launches": 3 * args.steps,
         "clocks": clocks,
     }
-    print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+    return line
+
+
+def run_extras(args, tsx, pk):
+    """The library's other workloads, a few steps each, summarized for the
+    headline line (one GPU)."""
+    import copy
+    out = {}
+
+    def sub(**kw):
+        a = copy.copy(args)
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a
+
+    keep = ("metric", "value", "unit", "ms_per_step", "steps", "warmup", "config", "roofline", "e2e",
+            "gpu_launches", "clocks")
+    for name, fn, kw, more in (
+            ("batch32", run_batch, dict(steps=3, warmup=3, tune=True, e2e_steps=1),
+             ("serial_ms_per_step", "batch_speedup_vs_serial", "decodes_per_s", "n_ts")),
+            ("serve", run_serve, dict(jobs=120, load=0.8),
+             ("p50_ms", "p90_ms", "p99_ms", "mean_ms", "plain", "edge_updates_per_s", "makespan_ms",
+              "max_concurrent_jobs", "hbm_peak_bytes", "results_identical_to_plain")),
+            ("isfer", run_isfer, dict(steps=3, warmup=3, samples=1_000_000),
+             ("edge_updates_per_s", "fer_mean", "fails_per_step"))):
+        t0 = time.perf_counter()
+        try:
+            line = fn(sub(workload=name, **kw), pk) if fn is not run_serve else fn(sub(workload=name, **kw))
+            out[name] = {k: line[k] for k in keep + more if k in line}
+        except Exception as e:  # one workload's failure must not hide the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    return out
 
 
 def main():
     args = parse()
-    if args.workload == "isfer" and args.impl != "reference":
-        run_isfer(args)
-        return
-    if args.workload == "serve" and args.impl != "reference":
-        run_serve(args)
-        return
-    if args.workload == "batch32" and args.impl != "reference":
-        run_batch(args)
-    elif args.impl == "reference":
+    line = None
+    if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "isfer":
+        line = run_isfer(args)
+    elif args.workload == "serve":
+        line = run_serve(args)
+    elif args.workload == "batch32":
+        line = run_batch(args)
     else:
         run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

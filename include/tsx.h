@@ -99,6 +99,37 @@ TSX_API int load_code(const tsx_code_desc *desc, void *stream, tsx_code **out);
 TSX_API void free_code(tsx_code *code);
 TSX_API int code_info(const tsx_code *code, tsx_code_info *info);
 
+/* ---- cycles and EMD spectrum (Sec. II, Prop. 1, Tables II and V) ---- */
+/* Cycles of length 4 and 6 through every variable node (computed once by
+ * load_code(): Table V's cycle densities per node).  c4, c6: host arrays of
+ * n entries.  Errors: TSX_EINVAL. */
+TSX_API int cycle_counts(const tsx_code *code, int64_t *c4, int64_t *c6);
+
+/* The EMD spectrum of Sec. II (Table II).  A cycle of length 2l is an
+ * exponent chain that closes (Prop. 1, eq. 3): a closed walk
+ * v0 - c1 - v1 - ... - c_l - v0 of the Tanner graph that never steps straight
+ * back (consecutive checks differ, consecutive variable nodes differ, c_l !=
+ * c_1), taken up to rotation and reversal; it may pass a node twice (the
+ * 4-cycle walked twice is an 8-cycle).  Its EMD is the number of checks
+ * connected to exactly one of its variable nodes.  The walks are enumerated
+ * from the orbit representatives (QC: the column index of a node is the
+ * running alternating sum of the exponents, and a walk closes when it is
+ * 0 mod Z) for l = 2 .. lmax (lmax <= 6).  count2l[l][e] / (2l) is the
+ * number of cycles of length 2l with EMD e -- per circulant orbit for a QC
+ * code (Table II's count "without multiplication by graph automorphism"), a
+ * plain count for a general code; it is fractional for a cycle invariant
+ * under part of the shift group.  walks[l]: closed walks from the
+ * representatives.  Synchronizes `stream`; allocates a few KB.  Errors:
+ * TSX_EINVAL (lmax), TSX_EUNSUPPORTED (search above ~4e11 walk steps),
+ * TSX_ENOMEM, TSX_ECUDA. */
+typedef struct {
+    int32_t lmax;
+    int64_t walks[7];
+    int64_t count2l[7][128];
+    double ms;             /* device time of the search (CUDA events) */
+} tsx_emd_spectrum;
+TSX_API int emd_spectrum(tsx_code *code, int32_t lmax, void *stream, tsx_emd_spectrum *out);
+
 /* ---- trapping-set enumeration (Sec. III) ----------------------------- */
 typedef struct tsx_ts_list tsx_ts_list;
 
@@ -133,6 +164,21 @@ typedef struct {
                               two posterior buffers do not fit: one buffer rebuilt by a
                               variable-node pass), else one codeword per group; the results
                               are the same */
+    int32_t list_mode;     /* 1 (min-sum decoders): the ordered list of Sec. III -- every non-empty
+                              S1(x_k) = Tree(X_k) and S2(x_k) = Tree(TS(X_k)), X_k = supp(x_k) u I,
+                              of the decode at the threshold amplitude, k = kstart .. K_last, is a
+                              trapping set; per set, count = candidates whose list holds it (each
+                              candidate counted once) and flags bits 1-2 = which of S1 / S2 gave it.
+                              Run as a second stage over the failing candidates only; per candidate
+                              cand_ts = -1 and cand_flags = 0.  K <= 1000. */
+    int32_t kstart;        /* list mode: first iteration of the list; 0 = max(1, floor(girth/2)),
+                              -1 = ceil(average iterations of the decodes of the first stage that
+                              converged to the all-zero word) (at least 1), > 0 as given */
+    int32_t budget_wref;   /* 0: every candidate gets K iterations.  > 0: cycle-density budget --
+                              candidate I gets K(I) = kmin + ceil((K - kmin) wref / (wref + W(I)))
+                              iterations, W(I) = sum over v in I of 2 c4(v) + c6(v), c4 / c6 the 4- and
+                              6-cycles through v (Sec. III, Table V) */
+    int32_t budget_kmin;   /* the smallest budget (1 <= kmin <= K) */
 } tsx_enum_params;
 
 /* Fills `p` with the defaults: NMS int16, K=20, base 16, sat 511, alpha 3/4,
@@ -163,7 +209,13 @@ typedef struct {
     double ms_total;       /* device time of the whole pipeline (CUDA events on the stream) */
     double ms_candidates;  /* candidate generation */
     double ms_decode;      /* the impulse-decoding kernel */
-    double ms_sieve;       /* extraction, classification, canonical form and dedupe */
+    double ms_sieve;       /* extraction, classification, canonical form and dedupe (list mode: the
+                              second stage -- its decodes, sieves and inserts) */
+    int64_t converged;     /* decodes that ended in the all-zero word */
+    int64_t converged_iterations; /* their iterations */
+    int64_t list_kstart;   /* list mode: the first iteration of the lists (0 otherwise) */
+    int64_t list_patterns; /* list mode: distinct x_k sieved (consecutive equal x_k are sieved once) */
+    int64_t list_iterations; /* list mode: iterations of the second stage's decodes */
 } tsx_enum_stats;
 
 /* Host views of the results, sorted by (a, b, key); valid until
@@ -424,6 +476,24 @@ TSX_API void server_destroy(tsx_server *server);
 TSX_API int decode_thresholds_noalloc(const tsx_code *code, const tsx_enum_params *params,
                                       const int32_t *cand_vars, int64_t n_cand, int32_t *thr, float *thr_f,
                                       int32_t *decodes, int32_t *iters, void *stream);
+
+/* ---- measured issue rates (no counterpart in the paper) ----------------
+ * The decoders are bound by integer issue and shared-memory bandwidth, for
+ * which no vendor figure is measured on the part.  measure_peaks() runs one
+ * short probe kernel per quantity with every SM full and reads each SM's
+ * cycle counter around its CTAs: the result is per SM clock (independent of
+ * the clock the GPU ran at), the median over SMs.  Multiply by the SM count
+ * and an SM clock to get a peak.  Synchronizes `stream`; allocates and frees
+ * a few KB of device memory.  Errors: TSX_EINVAL, TSX_ENOMEM, TSX_ECUDA. */
+typedef struct {
+    int32_t num_sms;               /* multiprocessors of the current device */
+    double int32_ops_per_clk_sm;   /* 32-bit integer lane operations (min.u32, xor) */
+    double u16x2_ops_per_clk_sm;   /* packed 16-bit lane operations (min.u16x2, xor): each serves two values */
+    double smem_bytes_per_clk_sm;  /* shared-memory load bytes (16-byte vector loads, no bank conflict) */
+    double sfu_ops_per_clk_sm;     /* special-function lane operations (ex2.approx.f32) */
+    double fp32_fma_per_clk_sm;    /* single-precision fused multiply-add lane operations */
+} tsx_peaks;
+TSX_API int measure_peaks(tsx_peaks *out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -56,7 +56,8 @@ class _IsParams(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("decoder", C.c_int), ("K", C.c_int), ("base_llr", C.c_int), ("sat", C.c_int),
                 ("alpha_num", C.c_int), ("alpha_shift", C.c_int), ("amp_steps", C.c_int),
-                ("spa_clip", C.c_float), ("spa_amax", C.c_float), ("list_mode", C.c_int), ("kstart", C.c_int)]
+                ("spa_clip", C.c_float), ("spa_amax", C.c_float), ("list_mode", C.c_int), ("kstart", C.c_int),
+                ("spa_libm", C.c_int), ("budget_wref", C.c_int), ("budget_kmin", C.c_int)]
 
 
 def lib():
@@ -96,7 +97,7 @@ def lib():
                                          C.POINTER(C.c_int)]
             L.og_decode_lnms.restype = C.c_int
             L.og_decode_spa.argtypes = [vp, F32P, C.c_int, C.c_float, C.c_int, U8P,
-                                        C.POINTER(C.c_int), I32P]
+                                        C.POINTER(C.c_int), I32P, C.c_int]
             L.og_decode_spa.restype = C.c_int
             L.og_spa_posterior.argtypes = [vp, F32P, C.c_int, C.c_float, F32P]
             L.og_tree.argtypes = [vp, U8P]
@@ -113,6 +114,9 @@ def lib():
             L.og_res_ts.argtypes = [vp, C.c_int, I32P, C.POINTER(C.c_float), I32P]
             L.og_res_ts.restype = C.c_int
             L.og_res_free.argtypes = [vp]
+            I64P = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+            L.og_res_stats.argtypes = [vp, I64P]
+            L.og_cycles_from.argtypes = [vp, C.c_int, C.c_int, I64P, vp]
             L.og_tanhf.argtypes = [C.c_float]
             L.og_tanhf.restype = C.c_float
             L.og_atanhf.argtypes = [C.c_float]
@@ -198,6 +202,9 @@ class Enumeration:
     decodes: np.ndarray   # int32 [N]
     iters: np.ndarray     # int32 [N], iterations summed over the candidate's decodes
     ts_list: list
+    converged: int = 0    # decodes that ended in the all-zero word
+    converged_iterations: int = 0
+    kstart: int = 0       # list mode: the first iteration of the lists
 
 
 class Graph:
@@ -286,13 +293,13 @@ class Graph:
                                  C.byref(kl))
         return bool(f), x, kl.value
 
-    def decode_spa(self, Lv, K, clip=30.0, wstart=None):
+    def decode_spa(self, Lv, K, clip=30.0, wstart=None, libm=False):
         Lv = np.ascontiguousarray(np.asarray(Lv, dtype=np.float32))
         ws = max(1, self.girth() // 2) if wstart is None else wstart
         xb = np.zeros(self.n, dtype=np.uint8)
         kl = C.c_int()
         ut = np.zeros(K + 1, dtype=np.int32)
-        f = lib().og_decode_spa(self.h, Lv, K, clip, ws, xb, C.byref(kl), ut)
+        f = lib().og_decode_spa(self.h, Lv, K, clip, ws, xb, C.byref(kl), ut, 1 if libm else 0)
         return bool(f), xb, kl.value, ut[: kl.value + 1]
 
     def spa_posterior(self, Lv, K, clip=30.0):
@@ -352,20 +359,49 @@ class Graph:
         lib().og_is_channel(self.h, Ta, Ta.size, C.byref(p), int(sample), L, nv)
         return L, nv
 
+    # --- cycles -----------------------------------------------------------
+    def cycle_walks(self, v, lmax, emd=False):
+        """Closed walks from v around simple cycles of l = 2..lmax variable
+        nodes (each cycle through v twice, one per direction): walks[l], and
+        with emd, hist[l, e] by the cycle's EMD e."""
+        walks = np.zeros(lmax + 1, dtype=np.int64)
+        hist = np.zeros((lmax + 1) * 128, dtype=np.int64) if emd else None
+        lib().og_cycles_from(self.h, int(v), int(lmax), walks,
+                             hist.ctypes.data_as(C.c_void_p) if emd else None)
+        return (walks, hist.reshape(lmax + 1, 128)) if emd else walks
+
+    def emd_spectrum(self, lmax, starts=None):
+        """Sum over the start nodes (QC: the orbit representatives (j,0);
+        general: every node) of the closed walks by length and EMD; dividing
+        by 2l gives cycles per circulant orbit (QC) or cycles (general)."""
+        if starts is None:
+            starts = [j * self.Z for j in range(self.n // self.Z)] if self.Z else range(self.n)
+        hist = np.zeros((lmax + 1, 128), dtype=np.int64)
+        walks = np.zeros(lmax + 1, dtype=np.int64)
+        for v in starts:
+            w, h = self.cycle_walks(v, lmax, emd=True)
+            hist += h
+            walks += w
+        return walks, hist
+
     # --- the whole method -----------------------------------------------
     def enumerate(self, cands=None, *, decoder="nms", K=20, base_llr=16, sat=511, alpha_num=3,
                   alpha_shift=2, amp_steps=10, spa_clip=30.0, spa_amax=64.0, max_size=3,
-                  cycle_len=0, list_mode=False, kstart=0) -> Enumeration:
+                  cycle_len=0, list_mode=False, kstart=0, spa_libm=False, budget_wref=0,
+                  budget_kmin=1) -> Enumeration:
         """list_mode (min-sum): every non-empty set of the ordered list S1(x_k),
-        S2(x_k), k = kstart (0: floor(girth/2)) .. K_last, of the decode at the
-        threshold is a trapping set; per trapping set, count = candidates whose
-        list holds it and kind = 1 (S1), 2 (S2) or 3 (both); the per-candidate
-        ts index is -1 in this mode."""
+        S2(x_k), k = kstart (0: floor(girth/2); -1: ceil of the average
+        iterations of the converged decodes of a first stage) .. K_last, of the
+        decode at the threshold is a trapping set; per trapping set, count =
+        candidates whose list holds it and kind = 1 (S1), 2 (S2) or 3 (both);
+        the per-candidate ts index is -1 in this mode.  budget_wref > 0: the
+        cycle-density iteration budget of each candidate."""
         if cands is None:
             cands = self.candidates(max_size, cycle_len)
         cands = np.ascontiguousarray(np.asarray(cands, dtype=np.int32).reshape(-1, 5))
         p = _Params(0 if decoder == "nms" else 1, K, base_llr, sat, alpha_num, alpha_shift,
-                    amp_steps, spa_clip, spa_amax, 1 if list_mode else 0, kstart)
+                    amp_steps, spa_clip, spa_amax, 1 if list_mode else 0, kstart, 1 if spa_libm else 0,
+                    budget_wref, budget_kmin)
         L = lib()
         h = L.og_enumerate(self.h, C.byref(p), cands, cands.shape[0])
         N = cands.shape[0]
@@ -383,5 +419,7 @@ class Graph:
             out.append(TS(a=int(info[0]), b=int(info[1]), key=tuple(int(x) for x in key[:a]),
                           orbit=int(info[2]), elementary=bool(info[3]), count=int(info[4]),
                           thr=int(info[5]), thr_f=float(tf.value), kind=int(info[6])))
+        st = np.zeros(3, dtype=np.int64)
+        L.og_res_stats(h, st)
         L.og_res_free(h)
-        return Enumeration(cands, thr, thr_f, ts, which, dec, it, out)
+        return Enumeration(cands, thr, thr_f, ts, which, dec, it, out, int(st[0]), int(st[1]), int(st[2]))

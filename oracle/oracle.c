@@ -185,6 +185,101 @@ int og_ball4(const og_graph *g, int v, int *out) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Cycles and their EMD (Sec. II, Table II; cycle density, Table V)     */
+/* ------------------------------------------------------------------ */
+
+/* Sec. II, Prop. 1 and Table II.  A "cycle" of length 2l is read as an
+ * exponent chain that closes (eq. 3), i.e. a closed walk
+ * v0 - c1 - v1 - ... - v_{l-1} - c_l - v0 of the Tanner graph that never
+ * steps straight back (c_{t+1} != c_t, v_{t+1} != v_t, and c_l != c_1), taken
+ * up to rotation and reversal; it may pass a node twice (the 4-cycle walked
+ * twice is an 8-cycle of Table II's EMD-2 row).  Its EMD is the number of
+ * check nodes connected to exactly one variable node of the walk.
+ *
+ * A walk class with rotation period p (smallest p with v_{t+p} = v_t and
+ * c_{t+p} = c_t) has p rotations, times 2 directions unless its reverse is
+ * one of them (r = 1 or 2), so it is met p r times as a walk from a start
+ * node; each walk adds 2l / (p r) to hist2[l][EMD], and hist2 / (2l) summed
+ * over every start node counts classes (over the orbit representatives of a
+ * QC code it counts classes per circulant orbit, Table II's "without
+ * multiplication by graph automorphism").  For l <= 3 every such walk is a
+ * simple cycle, and walks[l] from v is twice the cycles through v. */
+static int og_walk_emd(const og_graph *g, const int *vs, int L) {
+    int u[16], nu = 0;
+    for (int x = 0; x < L; x++) {
+        int dup = 0;
+        for (int y = 0; y < nu; y++) dup |= u[y] == vs[x];
+        if (!dup) u[nu++] = vs[x];
+    }
+    int emd = 0;
+    for (int x = 0; x < nu; x++)
+        for (int i = 0; i < g->vdeg[u[x]]; i++) {
+            int c = g->vadj[u[x] * g->dvmax + i], k = 0;
+            for (int y = 0; y < nu; y++)
+                for (int p = 0; p < g->cdeg[c]; p++) k += g->cadj[c * g->dcmax + p] == u[y];
+            emd += k == 1;
+        }
+    return emd;
+}
+
+/* p r of the closed walk vs[0..L-1], cs[1..L] (cs[t] between vs[t-1] and vs[t mod L]) */
+static int og_walk_reps(const int *vs, const int *cs, int L) {
+    int p = L;
+    for (int q = 1; q < L; q++) {
+        if (L % q) continue;
+        int ok = 1;
+        for (int t = 0; t < L && ok; t++) ok = vs[(t + q) % L] == vs[t] && cs[(t + q) % L + 1] == cs[t + 1];
+        if (ok) { p = q; break; }
+    }
+    /* reversed: v0, c_L, v_{L-1}, c_{L-1}, ...; rotated by s it equals the walk if
+     * v_{(s-t) mod L} = v_t and the check after it, c_{(s-t) mod L} (c_0 = c_L), = c_{t+1} */
+    int r = 2;
+    for (int sft = 0; sft < L && r == 2; sft++) {
+        int ok = 1;
+        for (int t = 0; t < L && ok; t++) {
+            int a = ((sft - t) % L + L) % L;
+            ok = vs[a] == vs[t] && cs[a == 0 ? L : a] == cs[t + 1];
+        }
+        if (ok) r = 1;
+    }
+    return p * r;
+}
+
+static void walks_from(const og_graph *g, int lmax, int d, int *vs, int *cs, long long *walks, long long *hist2) {
+    int v = vs[d];
+    for (int i = 0; i < g->vdeg[v]; i++) {
+        int c = g->vadj[v * g->dvmax + i];
+        if (d >= 1 && c == cs[d]) continue;  /* no step straight back */
+        if (d >= 1 && c != cs[1] && v != vs[0]) {
+            int closes = 0;
+            for (int p = 0; p < g->cdeg[c]; p++) closes |= g->cadj[c * g->dcmax + p] == vs[0];
+            if (closes) {
+                cs[d + 1] = c;
+                walks[d + 1]++;
+                if (hist2) hist2[(d + 1) * 128 + og_walk_emd(g, vs, d + 1)] += 2 * (d + 1) / og_walk_reps(vs, cs, d + 1);
+            }
+        }
+        if (d + 1 >= lmax) continue;
+        for (int p = 0; p < g->cdeg[c]; p++) {
+            int u = g->cadj[c * g->dcmax + p];
+            if (u == v) continue;
+            cs[d + 1] = c;
+            vs[d + 1] = u;
+            walks_from(g, lmax, d + 1, vs, cs, walks, hist2);
+        }
+    }
+}
+
+/* The closed walks from v of l = 2..lmax variable nodes (as above):
+ * walks[l] (lmax + 1 entries) and, if hist2 is not NULL, hist2[l * 128 + e]
+ * += 2l / (p r) per walk.  Both are added to. */
+void og_cycles_from(const og_graph *g, int v, int lmax, long long *walks, long long *hist2) {
+    int vs[16], cs[17];
+    vs[0] = v;
+    walks_from(g, lmax, 0, vs, cs, walks, hist2);
+}
+
+/* ------------------------------------------------------------------ */
 /* Canonical form under the circulant shift (graph automorphism)       */
 /* ------------------------------------------------------------------ */
 
@@ -573,8 +668,15 @@ float og_atanhf(float p) {
  *   var:    P_v = L_v + r(c_0->v) + r(c_1->v) + ... (checks ascending);
  *           q(v->c) = clip(P_v - r(c->v)); x_v = [P_v < 0]
  * Single precision, as the workload states. */
+/* libm = 1: the check update uses the C library's tanhf / atanhf instead of
+ * the series above (the other reading of the single-precision decoder: any
+ * correctly implemented tanh/atanh; thresholds then agree within the stated
+ * tolerance rather than bit for bit). */
+static float spa_tanh(float x, int libm) { return libm ? tanhf(x) : og_tanhf(x); }
+static float spa_atanh(float x, int libm) { return libm ? atanhf(x) : og_atanhf(x); }
+
 int og_decode_spa(const og_graph *g, const float *L, int K, float clip, int wstart,
-                  unsigned char *xbest, int *K_last, int *u_trace) {
+                  unsigned char *xbest, int *K_last, int *u_trace, int libm) {
     int E = g->m * g->dcmax;
     float *q = (float *)malloc(sizeof(float) * E), *r = (float *)malloc(sizeof(float) * E);
     float *t = (float *)malloc(sizeof(float) * g->dcmax);
@@ -589,13 +691,13 @@ int og_decode_spa(const og_graph *g, const float *L, int K, float clip, int wsta
     for (int k = 1; k <= K && u != 0; k++) {
         for (int c = 0; c < g->m; c++) {
             int d = g->cdeg[c];
-            for (int p = 0; p < d; p++) t[p] = og_tanhf(q[c * g->dcmax + p] * 0.5f);
+            for (int p = 0; p < d; p++) t[p] = spa_tanh(q[c * g->dcmax + p] * 0.5f, libm);
             for (int p = 0; p < d; p++) {
                 float prod = 1.0f;
                 for (int p2 = 0; p2 < d; p2++) if (p2 != p) prod = prod * t[p2];
                 float rr;
                 if (fabsf(prod) >= 1.0f) rr = prod > 0.0f ? clip : -clip;
-                else rr = 2.0f * og_atanhf(prod);
+                else rr = 2.0f * spa_atanh(prod, libm);
                 r[c * g->dcmax + p] = clampf(rr, -clip, clip);
             }
         }
@@ -758,6 +860,8 @@ typedef struct {
     float spa_amax; /* sum-product: amplitude range in LLR units */
     int list_mode;  /* 1: every set of the ordered list S1(x_k), S2(x_k), k = kstart..K_last */
     int kstart;     /* first iteration of that list; 0 = floor(girth / 2) (at least 1) */
+    int spa_libm;   /* sum-product with the C library's tanhf / atanhf */
+    int budget_wref, budget_kmin; /* cycle-density iteration budget (wref 0 = off) */
 } og_params;
 
 typedef struct {
@@ -778,6 +882,10 @@ typedef struct {
     /* distinct trapping sets sorted by (a, b, key) */
     int nts;
     og_ts *list;
+    /* decodes that converged to the all-zero word and their iterations; the
+     * first iteration of the lists in list mode */
+    long long ok_decodes, ok_iters;
+    int kstart_used;
 } og_result;
 
 typedef struct { int a, b, orbit, elem, kind, thr, cand; float thr_f; int *key; } ts_hit;
@@ -797,10 +905,54 @@ static int cmp_hit(const void *pa, const void *pb) {
  * failure there means no threshold), then up to s halvings of [lo, hi]
  * keeping the failing end; the threshold is the final hi and the trapping
  * set comes from the decode at that hi. */
+static og_result *og_enumerate_stage(og_graph *g, const og_params *pp, const int *cands, size_t ncand);
+void og_res_free(og_result *R);
+
+/* Iteration budgets (Sec. III: the number of iterations varied with the
+ * density of cycles through the symbol nodes; short-cycle trapping sets fail
+ * within fewer iterations).  Reading: candidate I gets
+ *   K(I) = kmin + ceil((K - kmin) * wref / (wref + W(I))),
+ *   W(I) = sum over v in I of 2 c4(v) + c6(v),
+ * c4(v) / c6(v) the 4- / 6-cycles through v (Table V's quantities per node);
+ * wref = 0 gives every candidate K. */
+static int *og_cycle_weights(const og_graph *g) {
+    int *w = (int *)malloc(sizeof(int) * g->n);
+    for (int v = 0; v < g->n; v++) {
+        long long walks[4] = {0, 0, 0, 0};
+        og_cycles_from(g, v, 3, walks, NULL);
+        /* a cycle through v is walked twice: 2 c4 + c6 = walks4 + walks6 / 2 */
+        w[v] = (int)(walks[2] + walks[3] / 2);
+    }
+    return w;
+}
+
+/* The enumeration.  In list mode with kstart = -1 it runs in two stages, as
+ * the paper's scheduler does: first the impulse decodes of every candidate
+ * (which gives the average iteration count of the decodes that converged),
+ * then the ordered lists from iteration ceil(average) on. */
 og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* ncand x 5 */,
                         size_t ncand) {
+    if (!(pp->list_mode && pp->kstart < 0)) return og_enumerate_stage(g, pp, cands, ncand);
+    og_params q = *pp;
+    q.list_mode = 0;
+    q.kstart = 0;
+    og_result *first = og_enumerate_stage(g, &q, cands, ncand);
+    int girth = og_girth(g), ks = girth / 2 > 1 ? girth / 2 : 1;
+    if (first->ok_decodes > 0) ks = (int)((first->ok_iters + first->ok_decodes - 1) / first->ok_decodes);
+    if (ks < 1) ks = 1;
+    og_res_free(first);
+    q = *pp;
+    q.kstart = ks;
+    og_result *R = og_enumerate_stage(g, &q, cands, ncand);
+    R->kstart_used = ks;
+    return R;
+}
+
+static og_result *og_enumerate_stage(og_graph *g, const og_params *pp, const int *cands, size_t ncand) {
     int girth = og_girth(g);
     int wstart = girth / 2 > 1 ? girth / 2 : 1;
+    int *vw = pp->budget_wref > 0 ? og_cycle_weights(g) : NULL;
+    long long ok = 0, okit = 0;
     og_result *R = (og_result *)calloc(1, sizeof(og_result));
     R->ncand = ncand;
     R->thr = (int *)malloc(sizeof(int) * ncand);
@@ -829,22 +981,31 @@ og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* nc
         int decodes = 0, iters = 0, kl, failed = 0, kl_keep = 0;
         int thr = -1;
         float thr_f = -1.0f;
+        int Kc = pp->K;
+        if (vw) {
+            long long W = 0;
+            for (int t = 0; t < nI; t++) W += vw[I[t]];
+            long long den = (long long)pp->budget_wref + W;
+            Kc = pp->budget_kmin + (int)(((long long)(pp->K - pp->budget_kmin) * pp->budget_wref + den - 1) / den);
+        }
         if (pp->decoder == 0) {
             int lo = 0, hi = (1 << pp->amp_steps) - 1;
             for (int v = 0; v < g->n; v++) Li[v] = clampi(pp->base_llr, -pp->sat, pp->sat);
             for (int t = 0; t < nI; t++) Li[I[t]] = clampi(pp->base_llr - hi, -pp->sat, pp->sat);
-            int f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL, NULL,
+            int f = og_decode_nms(g, Li, Kc, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL, NULL,
                                   list ? trace : NULL);
             decodes++; iters += kl;
+            if (!f) { ok++; okit += kl; }
             if (f) {
                 failed = 1; memcpy(keep, xb, g->n);
                 if (list) { memcpy(trace_keep, trace, (size_t)(kl + 1) * g->n); kl_keep = kl; }
                 for (int st = 0; st < pp->amp_steps && hi - lo > 1; st++) {
                     int mid = (lo + hi) >> 1;
                     for (int t = 0; t < nI; t++) Li[I[t]] = clampi(pp->base_llr - mid, -pp->sat, pp->sat);
-                    f = og_decode_nms(g, Li, pp->K, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL,
+                    f = og_decode_nms(g, Li, Kc, pp->sat, pp->alpha_num, pp->alpha_shift, wstart, xb, &kl, NULL,
                                       NULL, list ? trace : NULL);
                     decodes++; iters += kl;
+                    if (!f) { ok++; okit += kl; }
                     if (f) {
                         hi = mid; memcpy(keep, xb, g->n);
                         if (list) { memcpy(trace_keep, trace, (size_t)(kl + 1) * g->n); kl_keep = kl; }
@@ -856,15 +1017,17 @@ og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* nc
             float lo = 0.0f, hi = 1.0f, base = (float)pp->base_llr / 8.0f;
             for (int v = 0; v < g->n; v++) Lf[v] = clampf(base, -pp->spa_clip, pp->spa_clip);
             for (int t = 0; t < nI; t++) Lf[I[t]] = clampf(base - hi * pp->spa_amax, -pp->spa_clip, pp->spa_clip);
-            int f = og_decode_spa(g, Lf, pp->K, pp->spa_clip, wstart, xb, &kl, NULL);
+            int f = og_decode_spa(g, Lf, Kc, pp->spa_clip, wstart, xb, &kl, NULL, pp->spa_libm);
             decodes++; iters += kl;
+            if (!f) { ok++; okit += kl; }
             if (f) {
                 failed = 1; memcpy(keep, xb, g->n);
                 for (int st = 0; st < pp->amp_steps; st++) {
                     float mid = 0.5f * (lo + hi);
                     for (int t = 0; t < nI; t++) Lf[I[t]] = clampf(base - mid * pp->spa_amax, -pp->spa_clip, pp->spa_clip);
-                    f = og_decode_spa(g, Lf, pp->K, pp->spa_clip, wstart, xb, &kl, NULL);
+                    f = og_decode_spa(g, Lf, Kc, pp->spa_clip, wstart, xb, &kl, NULL, pp->spa_libm);
                     decodes++; iters += kl;
+                    if (!f) { ok++; okit += kl; }
                     if (f) { hi = mid; memcpy(keep, xb, g->n); } else lo = mid;
                 }
                 thr_f = hi;
@@ -939,12 +1102,19 @@ og_result *og_enumerate(og_graph *g, const og_params *pp, const int *cands /* nc
         free(hits[i].key);
     }
     R->nts = nts;
+    R->ok_decodes = ok;
+    R->ok_iters = okit;
+    R->kstart_used = list ? ks : 0;
     free(hits); free(Li); free(Lf); free(xb); free(keep); free(T); free(tv);
-    free(trace); free(trace_keep); free(X);
+    free(trace); free(trace_keep); free(X); free(vw);
     return R;
 }
 
 int og_res_nts(const og_result *R) { return R->nts; }
+/* ok_decodes, ok_iters, kstart_used */
+void og_res_stats(const og_result *R, long long *out) {
+    out[0] = R->ok_decodes; out[1] = R->ok_iters; out[2] = R->kstart_used;
+}
 void og_res_cand(const og_result *R, int *thr, float *thr_f, int *ts, int *which, int *decodes, int *iters) {
     memcpy(thr, R->thr, sizeof(int) * R->ncand);
     memcpy(thr_f, R->thr_f, sizeof(float) * R->ncand);

@@ -17,7 +17,9 @@ from ._tsx import (  # noqa: F401
     batch_stats,
     batch_view,
     code_info,
+    cycle_counts,
     decode_thresholds_noalloc,
+    emd_spectrum,
     enum_params_default,
     enumerate_ts,
     free_code,
@@ -27,6 +29,7 @@ from ._tsx import (  # noqa: F401
     lib,
     load_code,
     make_params,
+    measure_peaks,
     server_params_default,
     strerror,
     ts_list_stats,

@@ -51,14 +51,17 @@ class EnumParams(C.Structure):
                 ("spa_clip", C.c_float), ("spa_amax", C.c_float), ("max_size", C.c_int32),
                 ("cycle_len", C.c_int32), ("record_candidates", C.c_int32), ("cand_begin", C.c_int64),
                 ("cand_end", C.c_int64), ("warps_per_cta", C.c_int32), ("ctas_per_sm", C.c_int32),
-                ("kernel", C.c_int32)]
+                ("kernel", C.c_int32), ("list_mode", C.c_int32), ("kstart", C.c_int32), ("budget_wref", C.c_int32),
+                ("budget_kmin", C.c_int32)]
 
 
 class EnumStats(C.Structure):
     _fields_ = [("n_cand", C.c_int64), ("n_cand_total", C.c_int64), ("n_ts", C.c_int64),
                 ("decodes", C.c_int64), ("iterations", C.c_int64), ("edge_updates", C.c_int64),
                 ("acyclic", C.c_int64), ("ms_total", C.c_double), ("ms_candidates", C.c_double),
-                ("ms_decode", C.c_double), ("ms_sieve", C.c_double)]
+                ("ms_decode", C.c_double), ("ms_sieve", C.c_double), ("converged", C.c_int64),
+                ("converged_iterations", C.c_int64), ("list_kstart", C.c_int64), ("list_patterns", C.c_int64),
+                ("list_iterations", C.c_int64)]
 
 
 class IsParams(C.Structure):
@@ -96,6 +99,16 @@ class ServerStats(C.Structure):
                 ("max_ms", C.c_double), ("mean_ms", C.c_double), ("mean_queue_ms", C.c_double),
                 ("makespan_ms", C.c_double), ("edge_updates", C.c_int64), ("decodes", C.c_int64),
                 ("edge_updates_per_s", C.c_double), ("hbm_peak_bytes", C.c_int64), ("max_concurrent", C.c_int32)]
+
+
+class Peaks(C.Structure):
+    _fields_ = [("num_sms", C.c_int32), ("int32_ops_per_clk_sm", C.c_double), ("u16x2_ops_per_clk_sm", C.c_double),
+                ("smem_bytes_per_clk_sm", C.c_double), ("sfu_ops_per_clk_sm", C.c_double),
+                ("fp32_fma_per_clk_sm", C.c_double)]
+
+
+class EmdSpectrum(C.Structure):
+    _fields_ = [("lmax", C.c_int32), ("walks", C.c_int64 * 7), ("count2l", (C.c_int64 * 128) * 7), ("ms", C.c_double)]
 
 
 TSX_JOB_ENUMERATE, TSX_JOB_IS_FER = 0, 1
@@ -187,6 +200,12 @@ def lib():
             L.server_reset_stats.restype = None
             L.server_destroy.argtypes = [vp]
             L.server_destroy.restype = None
+            L.cycle_counts.argtypes = [vp, vp, vp]
+            L.cycle_counts.restype = C.c_int
+            L.emd_spectrum.argtypes = [vp, C.c_int32, vp, C.POINTER(EmdSpectrum)]
+            L.emd_spectrum.restype = C.c_int
+            L.measure_peaks.argtypes = [C.POINTER(Peaks), vp]
+            L.measure_peaks.restype = C.c_int
             _lib = L
     return _lib
 
@@ -579,3 +598,31 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def measure_peaks(stream=None) -> dict:
+    """measure_peaks(): per-SM-clock issue rates measured on the current device."""
+    p = Peaks()
+    _check(lib().measure_peaks(C.byref(p), _stream_handle(stream)), "measure_peaks")
+    return {k: getattr(p, k) for k, _ in Peaks._fields_}
+
+
+def cycle_counts(code: Code):
+    """cycle_counts(): the 4- and 6-cycles through every variable node (int64 arrays of n)."""
+    n = int(code.info["n"])
+    c4 = np.zeros(n, dtype=np.int64)
+    c6 = np.zeros(n, dtype=np.int64)
+    _check(lib().cycle_counts(code.h, c4.ctypes.data_as(C.c_void_p), c6.ctypes.data_as(C.c_void_p)), "cycle_counts")
+    return c4, c6
+
+
+def emd_spectrum(code: Code, lmax: int, stream=None) -> dict:
+    """emd_spectrum(): closed walks from the representatives per length
+    (walks[l]) and the class-weighted counts count2l[l, e]; count2l / (2l) is
+    the number of cycles of length 2l with EMD e (per circulant orbit for a QC
+    code)."""
+    out = EmdSpectrum()
+    _check(lib().emd_spectrum(code.h, int(lmax), _stream_handle(stream), C.byref(out)), "emd_spectrum")
+    walks = np.array(out.walks[:], dtype=np.int64)
+    count2l = np.array([row[:] for row in out.count2l], dtype=np.int64)
+    return {"lmax": int(out.lmax), "walks": walks, "count2l": count2l, "ms": float(out.ms)}

@@ -28,6 +28,11 @@ struct tsx_code {
     std::vector<int64_t> ball_ptr;  // host copy
     int device = 0;
     int num_sms = 0;
+    // cycles through each representative: closed walks of 2 and 3 variable
+    // nodes (twice the 4- and 6-cycles), and the iteration-budget weight
+    // 2 c4(v) + c6(v) of every variable node on the device
+    std::vector<int64_t> walks4, walks6;
+    int *vweight = nullptr;
 };
 
 struct tsx_ts_list {
@@ -338,11 +343,51 @@ extern "C" int load_code(const tsx_code_desc *desc, void *stream, tsx_code **out
         cudaFree(ball);
         return fail(TSX_ECUDA);
     }
+    // 4- and 6-cycles through the representatives (Table V's densities), for the iteration budgets
+    {
+        unsigned long long *walks = nullptr;
+        if (cudaMalloc(&walks, sizeof(unsigned long long) * n_rep * (kCycLmax + 1)) != cudaSuccess) {
+            cudaFree(ball);
+            return fail(TSX_ENOMEM);
+        }
+        std::vector<unsigned long long> hw((size_t)n_rep * (kCycLmax + 1));
+        if (launch_cycles(d, 3, walks, nullptr, s) != cudaSuccess ||
+            cudaMemcpyAsync(hw.data(), walks, sizeof(unsigned long long) * hw.size(), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaFree(walks);
+            cudaFree(ball);
+            return fail(TSX_ECUDA);
+        }
+        cudaFree(walks);
+        c->walks4.resize(n_rep);
+        c->walks6.resize(n_rep);
+        for (int r = 0; r < n_rep; r++) {
+            c->walks4[r] = (int64_t)hw[(size_t)r * (kCycLmax + 1) + 2];
+            c->walks6[r] = (int64_t)hw[(size_t)r * (kCycLmax + 1) + 3];
+        }
+        std::vector<int> vw(h.n);
+        for (int v = 0; v < h.n; v++) {
+            const int r = h.kind == TSX_CODE_QC ? v / h.Z : v;
+            const int64_t w = c->walks4[r] + c->walks6[r] / 2;
+            vw[v] = (int)std::min<int64_t>(w, 1 << 28);
+        }
+        if (cudaMalloc(&c->vweight, sizeof(int) * h.n) != cudaSuccess) {
+            cudaFree(ball);
+            return fail(TSX_ENOMEM);
+        }
+        if (cudaMemcpyAsync(c->vweight, vw.data(), sizeof(int) * h.n, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaFree(c->vweight);
+            cudaFree(ball);
+            return fail(TSX_ECUDA);
+        }
+    }
     tsx_code_info &in = c->info;
     in.kind = h.kind; in.n = h.n; in.m = h.m; in.E = h.E; in.Z = h.Z; in.n_b = h.n_b; in.m_b = h.m_b;
     in.dv_max = h.dv_max; in.dc_max = h.dc_max; in.girth = girth; in.n_rep = n_rep;
     in.ball_total = c->ball_ptr[n_rep];
-    in.device_bytes = (int64_t)blob.size() + sizeof(int32_t) * in.ball_total;
+    in.device_bytes = (int64_t)blob.size() + sizeof(int32_t) * (in.ball_total + h.n);
     *out = c;
     return TSX_OK;
 }
@@ -350,8 +395,59 @@ extern "C" int load_code(const tsx_code_desc *desc, void *stream, tsx_code **out
 extern "C" void free_code(tsx_code *c) {
     if (!c) return;
     cudaFree((void *)c->d.ball);
+    cudaFree(c->vweight);
     cudaFree(c->dev);
     delete c;
+}
+
+extern "C" int cycle_counts(const tsx_code *c, int64_t *c4, int64_t *c6) {
+    if (!c || !c4 || !c6) return TSX_EINVAL;
+    const DevCode &d = c->d;
+    for (int v = 0; v < d.n; v++) {
+        const int r = d.kind == TSX_CODE_QC ? v / d.Z : v;
+        c4[v] = c->walks4[r] / 2;
+        c6[v] = c->walks6[r] / 2;
+    }
+    return TSX_OK;
+}
+
+extern "C" int emd_spectrum(tsx_code *c, int32_t lmax, void *stream, tsx_emd_spectrum *out) {
+    if (!c || !out || lmax < 2 || lmax > kCycLmax) return TSX_EINVAL;
+    memset(out, 0, sizeof(*out));
+    const DevCode &d = c->d;
+    // walk nodes of the search: n_rep dv (dc - 1) ((dv - 1)(dc - 1))^(lmax - 2)
+    double work = (double)d.n_rep * d.dv_max * std::max(1, d.dc_max - 1);
+    for (int l = 2; l < lmax; l++) work *= (double)std::max(1, d.dv_max - 1) * std::max(1, d.dc_max - 1);
+    if (work > 4e11) return TSX_EUNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *buf = nullptr;
+    const size_t nw = (size_t)d.n_rep * (kCycLmax + 1), nh = (size_t)(kCycLmax + 1) * kEmdBins;
+    if (cudaMalloc(&buf, sizeof(unsigned long long) * (nw + nh)) != cudaSuccess) return TSX_ENOMEM;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<unsigned long long> hw(nw), hh(nh);
+    int st = TSX_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+        cudaEventRecord(e0, s) != cudaSuccess || launch_cycles(d, lmax, buf, buf + nw, s) != cudaSuccess ||
+        cudaEventRecord(e1, s) != cudaSuccess ||
+        cudaMemcpyAsync(hw.data(), buf, sizeof(unsigned long long) * nw, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(hh.data(), buf + nw, sizeof(unsigned long long) * nh, cudaMemcpyDeviceToHost, s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        st = TSX_ECUDA;
+    if (st == TSX_OK) {
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        out->ms = ms;
+        out->lmax = lmax;
+        for (size_t r = 0; r < (size_t)d.n_rep; r++)
+            for (int l = 2; l <= lmax; l++) out->walks[l] += (int64_t)hw[r * (kCycLmax + 1) + l];
+        for (int l = 2; l <= lmax; l++)
+            for (int e = 0; e < kEmdBins; e++) out->count2l[l][e] = (int64_t)hh[(size_t)l * kEmdBins + e];
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(buf);
+    return st;
 }
 
 extern "C" int code_info(const tsx_code *c, tsx_code_info *info) {
@@ -402,6 +498,11 @@ static int check_params(const tsx_enum_params &p) {
     if (p.cand_end >= 0 && p.cand_end < p.cand_begin) return TSX_EINVAL;
     if (p.warps_per_cta < 0 || p.warps_per_cta > 16 || p.ctas_per_sm < 0) return TSX_EINVAL;
     if (p.kernel < 0 || p.kernel > 2) return TSX_EINVAL;
+    if (p.list_mode < 0 || p.list_mode > 1 || p.kstart < -1) return TSX_EINVAL;
+    if (p.list_mode && p.decoder == TSX_DEC_SPA_F32) return TSX_EUNSUPPORTED;
+    if (p.list_mode && p.K > 1000) return TSX_EUNSUPPORTED;
+    if (p.budget_wref < 0) return TSX_EINVAL;
+    if (p.budget_wref > 0 && (p.budget_kmin < 1 || p.budget_kmin > p.K)) return TSX_EINVAL;
     return TSX_OK;
 }
 
@@ -416,6 +517,7 @@ int enum_params_to_decode(const tsx_enum_params *p, DecodeParams *dp) {
     dp->decoder = p->decoder; dp->K = p->K; dp->base_llr = p->base_llr; dp->sat = p->sat;
     dp->alpha_num = p->alpha_num; dp->alpha_shift = p->alpha_shift; dp->amp_steps = p->amp_steps;
     dp->spa_clip = p->spa_clip; dp->spa_amax = p->spa_amax;
+    dp->budget_wref = 0; dp->budget_kmin = 0; dp->vweight = nullptr;
     return TSX_OK;
 }
 }  // namespace tsx
@@ -493,6 +595,7 @@ static int prepare_list(tsx_code *code, const tsx_enum_params *params, cudaStrea
     if (n_rec < 0) n_rec = 0;
 
     if (!decode_fits(g, p.decoder)) return TSX_EUNSUPPORTED;
+    if (p.list_mode && !list_fits(g, p.K)) return TSX_EUNSUPPORTED;
 
     tsx_ts_list *L = new tsx_ts_list();
     L->dry = dry;
@@ -512,13 +615,16 @@ static int prepare_list(tsx_code *code, const tsx_enum_params *params, cudaStrea
     L->cycles = cycles;
     L->cyc_l = l;
     L->paths = paths;
-    L->cap = next_pow2(std::max<long long>(1024, 2 * std::max<long long>(n_rec, 1)));
-    L->pool_cap = std::max<long long>(1 << 20, 24 * n_rec);
+    // list mode: several sets per failing candidate
+    L->cap = next_pow2(std::max<long long>(1024, (p.list_mode ? 4 : 2) * std::max<long long>(n_rec, 1)));
+    L->pool_cap = std::max<long long>(1 << 20, (p.list_mode ? 48 : 24) * n_rec);
     if (L->pool_cap > 0xfffffff0LL) L->pool_cap = 0xfffffff0LL;
     DecodeParams &dp = L->dp;
     dp.decoder = p.decoder; dp.K = p.K; dp.base_llr = p.base_llr; dp.sat = p.sat;
     dp.alpha_num = p.alpha_num; dp.alpha_shift = p.alpha_shift; dp.amp_steps = p.amp_steps;
     dp.spa_clip = p.spa_clip; dp.spa_amax = p.spa_amax;
+    dp.budget_wref = p.budget_wref; dp.budget_kmin = p.budget_kmin;
+    dp.vweight = p.budget_wref > 0 ? code->vweight : nullptr;
 
     L->n_chunks = cand_chunks(raw_total);
     L->d_raw_off = lalloc<long long>(L, n_rep + 1, s);
@@ -551,7 +657,8 @@ static int prepare_list(tsx_code *code, const tsx_enum_params *params, cudaStrea
     b.ctr = L->ctr;
     b.queue = L->ctr ? &L->ctr->next_cand : nullptr;
     b.rec_base = p.cand_begin;
-    const long long ts_cap = std::min<long long>(L->cap, std::max<long long>(n_rec, 1));
+    // distinct sets: at most one per failing candidate, or (list mode) as many as the table holds
+    const long long ts_cap = p.list_mode ? L->cap : std::min<long long>(L->cap, std::max<long long>(n_rec, 1));
     L->ts_off = lalloc<int>(L, ts_cap, s);
     L->ts_count = lalloc<int>(L, ts_cap, s);
     L->ts_thr = lalloc<int>(L, ts_cap, s);
@@ -652,7 +759,11 @@ static int enqueue_decode(tsx_ts_list *L, cudaStream_t s) {
 // sieve, classification, dedupe, compaction
 static int enqueue_back(tsx_ts_list *L, cudaStream_t s) {
     if (record(L, 2, s) != TSX_OK) return TSX_ECUDA;
-    if (launch_sieve(L->code->d, L->b, L->p.decoder, L->grid_sms, s) != cudaSuccess) return TSX_ECUDA;
+    if (L->p.list_mode) {
+        if (launch_list(L->code->d, L->dp, L->b, L->p.kstart, L->grid_sms, s) != cudaSuccess) return TSX_ECUDA;
+    } else if (launch_sieve(L->code->d, L->b, L->p.decoder, L->grid_sms, s) != cudaSuccess) {
+        return TSX_ECUDA;
+    }
     if (record(L, 3, s) != TSX_OK) return TSX_ECUDA;
     if (launch_compact(L->b, L->n_rec, L->ts_off, L->ts_count, L->ts_thr, L->slot_map, s) != cudaSuccess)
         return TSX_ECUDA;
@@ -841,6 +952,10 @@ extern "C" int batch_stats(tsx_batch *B, tsx_enum_stats *total) {
         total->iterations += s.iterations;
         total->edge_updates += s.edge_updates;
         total->acyclic += s.acyclic;
+        total->converged += s.converged;
+        total->converged_iterations += s.converged_iterations;
+        total->list_patterns += s.list_patterns;
+        total->list_iterations += s.list_iterations;
     }
     return ret;
 }
@@ -861,6 +976,11 @@ static void fill_stats(tsx_ts_list *L, const Counters &c, tsx_enum_stats &s) {
     s.iterations = (int64_t)c.iterations;
     s.edge_updates = (int64_t)c.edge_updates;
     s.acyclic = (int64_t)c.acyclic;
+    s.converged = (int64_t)c.ok_decodes;
+    s.converged_iterations = (int64_t)c.ok_iters;
+    s.list_kstart = (int64_t)c.list_kstart;
+    s.list_patterns = (int64_t)c.list_patterns;
+    s.list_iterations = (int64_t)c.list_iters;
     float ms = 0.0f;
     if (L->ev[4] && cudaEventElapsedTime(&ms, L->ev[0], L->ev[4]) == cudaSuccess) s.ms_total = ms;
     if (L->ev[1] && cudaEventElapsedTime(&ms, L->ev[0], L->ev[1]) == cudaSuccess) s.ms_candidates = ms;

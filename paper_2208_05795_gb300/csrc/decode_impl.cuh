@@ -421,7 +421,8 @@ struct Decoder {
     }
 
     // Returns true if the decode failed (x_{K_last} != 0); xbest receives x*.
-    __device__ bool run(const int *I, int nI, lv Lbase, lv Limp, uint32_t *xbest, int &kl) const {
+    // K: the iteration limit of this candidate.
+    __device__ bool run(const int *I, int nI, lv Lbase, lv Limp, uint32_t *xbest, int &kl, int K) const {
         if (!(Limp < (lv)0)) {  // x_0 = 0: u_0 = 0, success at iteration 0
             kl = 0;
             return false;
@@ -433,13 +434,13 @@ struct Decoder {
         int ubest = 0x7fffffff, u = 0, k = 0;
         bool first = true;
         while (true) {
-            u = check_pass(first, k < dp.K);  // u = u_k; R <- R_{k+1}
+            u = check_pass(first, k < K);  // u = u_k; R <- R_{k+1}
             first = false;
             if (k >= g.wstart && u < ubest) {
                 ubest = u;
                 save_x(xbest);
             }
-            if (u == 0 || k == dp.K) break;
+            if (u == 0 || k == K) break;
             vn_pass(Lbase);  // P <- P_{k+1}
             gp.sync();
             if (gp.gt < nI) P[I[gp.gt]] = (post)posterior(I[gp.gt], Limp);
@@ -455,6 +456,16 @@ struct Decoder {
         return u != 0 || any != 0;
     }
 };
+
+// Iteration limit of candidate I: K, or with a cycle-density budget
+// kmin + ceil((K - kmin) wref / (wref + W(I))), W(I) = sum of vweight over I.
+__device__ __forceinline__ int cand_budget(const DecodeParams &dp, const int *I, int nI) {
+    if (dp.budget_wref <= 0) return dp.K;
+    long long W = 0;
+    for (int t = 0; t < nI; t++) W += dp.vweight[I[t]];
+    const long long den = (long long)dp.budget_wref + W;
+    return dp.budget_kmin + (int)(((long long)(dp.K - dp.budget_kmin) * dp.budget_wref + den - 1) / den);
+}
 
 // ---------------------------------------------------------------------------
 // sieving: Tree(), TS(), (a,b)
@@ -832,7 +843,7 @@ __device__ __forceinline__ void scalar_run(const DevCode &g, const DecodeParams 
 
     const long long total = (long long)b.ctr->n_cand_total;
     const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
-    long long my_dec = 0, my_it = 0, my_eu = 0;
+    long long my_dec = 0, my_it = 0, my_eu = 0, my_ok = 0, my_okit = 0;
 
     lv Lbase;
     if constexpr (Dec::kFloat) Lbase = (lv)clampf_((float)dp.base_llr / 8.0f, -dp.spa_clip, dp.spa_clip);
@@ -853,19 +864,22 @@ __device__ __forceinline__ void scalar_run(const DevCode &g, const DecodeParams 
         bool failed = false;
         int thr = -1;
         float thr_f = -1.0f;
+        const int Kc = cand_budget(dp, I, nI);
         if constexpr (!Dec::kFloat) {
             int lo = 0, hi = (1 << dp.amp_steps) - 1;
-            bool f = dec.run(I, nI, Lbase, (lv)clampi(dp.base_llr - hi, -dp.sat, dp.sat), xcur, kl);
+            bool f = dec.run(I, nI, Lbase, (lv)clampi(dp.base_llr - hi, -dp.sat, dp.sat), xcur, kl, Kc);
             ndec++;
             nit += kl;
+            if (!f) { my_ok++; my_okit += kl; }
             if (f) {
                 failed = true;
                 uint32_t *t = xcur; xcur = xkeep; xkeep = t;
                 for (int st = 0; st < dp.amp_steps && hi - lo > 1; st++) {
                     const int mid = (lo + hi) >> 1;
-                    f = dec.run(I, nI, Lbase, (lv)clampi(dp.base_llr - mid, -dp.sat, dp.sat), xcur, kl);
+                    f = dec.run(I, nI, Lbase, (lv)clampi(dp.base_llr - mid, -dp.sat, dp.sat), xcur, kl, Kc);
                     ndec++;
                     nit += kl;
+                    if (!f) { my_ok++; my_okit += kl; }
                     if (f) {
                         hi = mid;
                         uint32_t *t2 = xcur; xcur = xkeep; xkeep = t2;
@@ -881,17 +895,19 @@ __device__ __forceinline__ void scalar_run(const DevCode &g, const DecodeParams 
             auto limp = [&](float eps) {
                 return (lv)clampf_(__fsub_rn(basef, __fmul_rn(eps, dp.spa_amax)), -dp.spa_clip, dp.spa_clip);
             };
-            bool f = dec.run(I, nI, Lbase, limp(hi), xcur, kl);
+            bool f = dec.run(I, nI, Lbase, limp(hi), xcur, kl, Kc);
             ndec++;
             nit += kl;
+            if (!f) { my_ok++; my_okit += kl; }
             if (f) {
                 failed = true;
                 uint32_t *t = xcur; xcur = xkeep; xkeep = t;
                 for (int st = 0; st < dp.amp_steps; st++) {
                     const float mid = __fmul_rn(0.5f, __fadd_rn(lo, hi));
-                    f = dec.run(I, nI, Lbase, limp(mid), xcur, kl);
+                    f = dec.run(I, nI, Lbase, limp(mid), xcur, kl, Kc);
                     ndec++;
                     nit += kl;
+                    if (!f) { my_ok++; my_okit += kl; }
                     if (f) {
                         hi = mid;
                         uint32_t *t2 = xcur; xcur = xkeep; xkeep = t2;
@@ -927,6 +943,8 @@ __device__ __forceinline__ void scalar_run(const DevCode &g, const DecodeParams 
         atomicAdd(&b.ctr->decodes, (unsigned long long)my_dec);
         atomicAdd(&b.ctr->iterations, (unsigned long long)my_it);
         atomicAdd(&b.ctr->edge_updates, (unsigned long long)my_eu);
+        atomicAdd(&b.ctr->ok_decodes, (unsigned long long)my_ok);
+        atomicAdd(&b.ctr->ok_iters, (unsigned long long)my_okit);
     }
 }
 

@@ -77,6 +77,7 @@ struct Half {
     int failed;
     int Limp;  // channel LLR of the impulse nodes in the current decode
     int k, ubest;
+    int K;      // iteration limit of the candidate
     int first;  // current decode has run no check pass yet
     int cur;    // x buffer of the current decode (0/1); keep = cur ^ 1
     __device__ __forceinline__ int Ik(int t) const { return t == 0 ? I0 : t == 1 ? I1 : t == 2 ? I2 : I3; }
@@ -532,7 +533,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
     const int Lb = clampi(dp.base_llr, -dp.sat, dp.sat);
     const int amax = (1 << dp.amp_steps) - 1;
-    long long my_dec = 0, my_it = 0;
+    long long my_dec = 0, my_it = 0, my_ok = 0, my_okit = 0;
     int pcur = 0;  // which posterior buffer holds P_k
 
     Half H[2];
@@ -546,6 +547,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         h.ubest = 0x7fffffff;
         h.first = 1;
         h.cur = 0;
+        h.K = dp.K;
         if (idx >= end) {
             h.idx = -1;
             h.nI = 0;
@@ -558,6 +560,12 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         h.lo = 0; h.hi = amax; h.st = 0; h.phase = 0;
         h.thr = -1; h.ndec = 0; h.nit = 0; h.failed = 0;
         h.Limp = clampi(dp.base_llr - amax, -dp.sat, dp.sat);
+        if (dp.budget_wref > 0) {
+            const int Iv[4] = {h.I0, h.I1, h.I2, h.I3};
+            h.K = cand_budget(dp, Iv, h.nI);
+        } else {
+            h.K = dp.K;
+        }
     };
     // finish the candidate of half hh (records, x* to global) and fetch the next
     auto finish = [&](Half &h, int hh) {
@@ -587,6 +595,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         while (h.idx >= 0) {
             if (h.Limp < 0) return true;
             h.ndec++;
+            my_ok++;  // x_0 = 0: converged at iteration 0
             if (h.phase == 0) {
                 finish(h, hh);  // no failure at the largest amplitude
                 continue;
@@ -649,7 +658,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         unsigned *Pc = VN ? Pbuf : Pbuf + pcur * g.n, *Pn = VN ? Pbuf : Pbuf + (pcur ^ 1) * g.n;
         const unsigned km = (H[0].first ? 0xFFFF0000u : 0xFFFFFFFFu) & (H[1].first ? 0x0000FFFFu : 0xFFFFFFFFu);
         const unsigned kb = pc.B2 & ~km;
-        const bool wr = (H[0].idx >= 0 && H[0].k < dp.K) || (H[1].idx >= 0 && H[1].k < dp.K);
+        const bool wr = (H[0].idx >= 0 && H[0].k < H[0].K) || (H[1].idx >= 0 && H[1].k < H[1].K);
         // u_k of both halves from P_k = Pc; Pn accumulates P_{k+1}
         const int us = km != 0xFFFFFFFFu ? dec.template check_pass<true>(km, kb, wr, Pc, Pn)
                                          : dec.template check_pass<false>(km, kb, wr, Pc, Pn);
@@ -663,13 +672,17 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
                 h.ubest = u;
                 dec.save_x(Pc, hh, xc);
             }
-            if (u != 0 && h.k != dp.K) continue;
+            if (u != 0 && h.k != h.K) continue;
             // the decode ended at K_last = k
             const int kl = h.k;
             if (kl < g.wstart) dec.save_x(Pc, hh, xc);
             const bool fail = u != 0 || dec.any_neg(Pc, hh) != 0;
             h.ndec++;
             h.nit += kl;
+            if (!fail) {
+                my_ok++;
+                my_okit += kl;
+            }
             if (h.phase == 0) {
                 if (!fail) {
                     finish(h, hh);
@@ -741,6 +754,8 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         atomicAdd(&b.ctr->decodes, (unsigned long long)my_dec);
         atomicAdd(&b.ctr->iterations, (unsigned long long)my_it);
         atomicAdd(&b.ctr->edge_updates, (unsigned long long)my_it * (unsigned long long)g.E);
+        atomicAdd(&b.ctr->ok_decodes, (unsigned long long)my_ok);
+        atomicAdd(&b.ctr->ok_iters, (unsigned long long)my_okit);
     }
 }
 

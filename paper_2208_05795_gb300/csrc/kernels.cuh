@@ -105,6 +105,24 @@ bool plan_is_shape(const DevCode &g, const DecodeParams &dp, LaunchShape *sh, in
 // Whether one codeword of g fits the shared memory of a CTA.
 bool decode_fits(const DevCode &g, int decoder);
 
+// ---- the ordered list of Sec. III (list.cu) --------------------------------
+// Whether one group's list-mode slot fits a CTA for iteration limit K.
+bool list_fits(const DevCode &g, int K);
+// The second stage over the failing candidates of b (after the decode):
+// replay at the threshold, sieve every x_k from kstart (0: floor(girth/2),
+// -1: ceil of the first stage's average converged iterations), insert.
+cudaError_t launch_list(const DevCode &g, const DecodeParams &dp, const EnumBuffers &b, int kstart, int num_sms,
+                        cudaStream_t st);
+
+// ---- short cycles (cycles.cu) ------------------------------------------------
+constexpr int kCycLmax = 6;     // variable nodes per cycle at most
+constexpr int kEmdBins = 128;   // EMD values per length
+// Closed walks from the representatives, per representative and number of
+// variable nodes (walks[n_rep][kCycLmax + 1]) and, with hist, per number of
+// variable nodes and EMD (hist[kCycLmax + 1][kEmdBins]); zeroed first.
+cudaError_t launch_cycles(const DevCode &g, int lmax, unsigned long long *walks, unsigned long long *hist,
+                          cudaStream_t st);
+
 // accessors of a loaded code (api.cu)
 const DevCode *code_dev(const tsx_code *c);
 int code_num_sms(const tsx_code *c);

@@ -65,6 +65,11 @@ struct Counters {
     unsigned long long n_fail;      // importance sampling: failing samples
     unsigned long long pool_leaked; // key-pool words reserved by an insert that lost to an equal key
                                     // and could not be given back
+    unsigned long long ok_decodes;  // decodes that ended in the all-zero word
+    unsigned long long ok_iters;    // their iterations
+    unsigned long long list_patterns;  // list mode: x_k patterns sieved
+    unsigned long long list_iters;     // list mode: iterations of the second stage
+    unsigned long long list_kstart;    // list mode: first iteration of the lists
     unsigned int n_ts;
     unsigned int err;               // bit flags, see kErr*
 };
@@ -85,6 +90,11 @@ constexpr int kPoolHdr = 4;
 struct DecodeParams {
     int decoder;  // TSX_DEC_*
     int K;
+    // cycle-density iteration budget: wref > 0 gives candidate I
+    // kmin + ceil((K - kmin) wref / (wref + W(I))) iterations, W(I) the sum of
+    // vweight over I
+    int budget_wref, budget_kmin;
+    const int *vweight;  // [n] 2 c4(v) + c6(v) (device), with wref > 0
     int base_llr;
     int sat;
     int alpha_num, alpha_shift;

@@ -27,7 +27,8 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == os.cpu_count()
+    assert d["cpu_baseline"]["nproc"] == os.cpu_count()
     assert d["config"]["workload"] == "qc96"
 
 
@@ -60,3 +61,16 @@ def test_served_launch_count():
     res = [{"enum_stats": {"n_cand": 40_000}}, {"enum_stats": {"n_cand": 0}}, {"enum_stats": {"n_cand": 700}}]
     # 3 + ceil(40000/16384) + 3 = 9; ceil(10^6/32768) + 2 = 33; 3 + 1 + 3 = 7
     assert bench.served_launches(jobs, res) == 9 + 33 + 7
+
+
+def test_alu_roofline_terms():
+    # two values per 16-bit-pair lane operation, 12 operations and 4 shared-memory bytes per edge update
+    pk = dict(num_sms=2, int32_ops_per_clk_sm=128.0, u16x2_ops_per_clk_sm=128.0, smem_bytes_per_clk_sm=128.0)
+    r = bench.alu_roofline(eu_per_launch=1e9, ms_launch=100.0, pk=pk, sm_mhz=1000.0)
+    clk = 2 * 1e9
+    assert r["terms"]["int_bound"] == 128 * clk * 2 / 12
+    assert r["terms"]["smem_bound"] == 128 * clk / 4
+    assert r["peak"] == min(r["terms"]["int_bound"], r["terms"]["smem_bound"])
+    assert r["achieved"] == 1e10 and abs(r["frac"] - 1e10 / r["peak"]) < 1e-12
+    r1 = bench.alu_roofline(1e9, 100.0, pk, 1000.0, packed=False)
+    assert r1["peak"] == 128 * clk / 12
