@@ -848,6 +848,108 @@ def run_isfer(args, pk=None):
     return line
 
 
+def _timed(fn, stream):
+    """Device milliseconds of fn() on `stream` (CUDA events), after a 256 MB L2 flush."""
+    import torch
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        flush.fill_(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def extra_list(tsx, pk, stream, steps=2):
+    """The ordered list of Sec. III on the 2640-node QC code (every canonical
+    candidate, K = 100): first stage (the enumeration decode) and second stage
+    (replay and sieve of every x_k from ceil(average converged iterations))."""
+    w = synth.workload("qc2640")
+    c = tsx.load_code(w["code"], stream=stream)
+    p = params_of(w, "nms16")
+    for _ in range(1):
+        tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, list_mode=1, kstart=-1, **p))
+    rows = []
+    for _ in range(steps):
+        ms, st = _timed(lambda: tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, list_mode=1, kstart=-1, **p)),
+                        stream)
+        rows.append((ms, st))
+    ms = statistics.median(r[0] for r in rows)
+    st = rows[-1][1]
+    single = tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, **p))
+    return {"workload": "qc2640 list mode (two-stage, kstart = ceil(avg))", "ms_per_step": ms,
+            "n_cand": st["n_cand"], "n_ts": st["n_ts"], "n_ts_single_pattern": single["n_ts"],
+            "distinct_ts_per_s": st["n_ts"] / (ms / 1e3), "list_kstart": st["list_kstart"],
+            "list_patterns": st["list_patterns"], "ms_first_stage": st["ms_decode"],
+            "ms_second_stage": st["ms_sieve"], "second_stage_iterations": st["list_iterations"],
+            "edge_updates_per_s": (st["edge_updates"] + st["list_iterations"] * w["code"].E) / (ms / 1e3),
+            "gpu_launches": 3 + 3 + 1 + 1 + 2}
+
+
+def extra_budget(tsx, pk, stream):
+    """Cycle-density iteration budgets (Sec. III, Table V) on the PEG code's
+    first 2 million candidates: K(I) = 10 + ceil(40 * 4 / (4 + W(I)))."""
+    w = synth.workload("peg1008")
+    c = tsx.load_code(w["code"], stream=stream)
+    p = dict(params_of(w, "nms16"), cand_end=2_000_000)
+    out = {}
+    for name, extra in (("plain", {}), ("budget", dict(budget_wref=4, budget_kmin=10))):
+        tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, **p, **extra))
+        ms, st = _timed(lambda: tsx.ts_list_view(tsx.enumerate_ts(c, stream=stream, **p, **extra)), stream)
+        out[name] = {"ms": ms, "edge_updates": st["stats"]["edge_updates"], "n_ts": st["stats"]["n_ts"],
+                     "keys": set(st["keys"])}
+    kp, kb = out["plain"].pop("keys"), out["budget"].pop("keys")
+    return {"workload": "peg1008[:2000000] with and without iteration budgets (wref 4, kmin 10)", **out,
+            "speedup": out["plain"]["ms"] / out["budget"]["ms"],
+            "sets_kept": len(kp & kb) / max(1, len(kp)), "sets_new": len(kb - kp)}
+
+
+def extra_lnms(tsx, pk, stream, sm_mhz):
+    """The paper's simulation decoder (layered min-sum, 4/4/6 bits, 20
+    iterations) on Code 1 of Table V ((2560, 2048), 4 x 20 base, Z = 128),
+    200,000 frames at Eb/N0 = 3 dB."""
+    E, Z = _code1()
+    c = tsx.load_code(synth.qc_code(E, Z), stream=stream)
+    kw = dict(ebn0_db=3.0, max_frames=200_000, max_errors=0)
+    tsx.lnms_simulate(c, stream=stream, job_key=1, **kw)
+    r = tsx.lnms_simulate(c, stream=stream, job_key=2, **kw)
+    return {"workload": "Code 1 (Table V), 200,000 frames, 3 dB, LLR/C2V/V2C 4/4/6 bits, 20 iterations",
+            "frames_per_s": r["frames"] / (r["ms"] / 1e3), "fer": r["fer"], "ber": r["ber"],
+            "edge_updates_per_s": r["edge_updates"] / (r["ms"] / 1e3), "ms": r["ms"],
+            "roofline": alu_roofline(r["edge_updates"], r["ms"], pk, sm_mhz, packed=False,
+                                     note="one frame per group, 8-bit values, scalar integer operations"),
+            "gpu_launches": -(-200_000 // 65536)}
+
+
+def extra_emd(tsx, stream):
+    """EMD spectrum of Code 1 (Table II) up to 12-cycles on the device."""
+    E, Z = _code1()
+    c = tsx.load_code(synth.qc_code(E, Z), stream=stream)
+    tsx.emd_spectrum(c, 5, stream=stream)
+    s = tsx.emd_spectrum(c, 6, stream=stream)
+    rows = {f"{2 * l}": {str(e): float(s["count2l"][l, e]) / (2 * l) for e in np.flatnonzero(s["count2l"][l])}
+            for l in range(2, 7)}
+    return {"workload": "Code 1 (Table V), cycles of length 4..12", "ms": s["ms"],
+            "walks": int(s["walks"].sum()), "spectrum_per_orbit": rows, "gpu_launches": 1}
+
+
+def _code1():
+    rows, Z = [], None
+    with open(os.path.join(ROOT, "tests", "golden", "code1_table5.txt")) as f:
+        for line in f:
+            t = line.split("#", 1)[0].split()
+            if not t:
+                continue
+            if t[0] == "Z":
+                Z = int(t[1])
+            elif t[0][0] in "-0123456789":
+                rows.append([int(x) for x in t])
+    return np.array(rows, dtype=np.int32), Z
+
+
 def run_extras(args, tsx, pk):
     """The library's other workloads, a few steps each, summarized for the
     headline line (one GPU)."""
@@ -875,6 +977,21 @@ def run_extras(args, tsx, pk):
             line = fn(sub(workload=name, **kw), pk) if fn is not run_serve else fn(sub(workload=name, **kw))
             out[name] = {k: line[k] for k in keep + more if k in line}
         except Exception as e:  # one workload's failure must not hide the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+    import torch
+    stream = torch.cuda.Stream()
+    sm = None
+    for name, fn in (("list_mode", lambda: extra_list(tsx, pk, stream)),
+                     ("iteration_budget", lambda: extra_budget(tsx, pk, stream)),
+                     ("layered_simulation", lambda: extra_lnms(tsx, pk, stream, sm)),
+                     ("emd_spectrum", lambda: extra_emd(tsx, stream))):
+        t0 = time.perf_counter()
+        try:
+            with Clocks(torch.cuda.current_device()) as clk:
+                out[name] = fn()
+            out[name]["clocks"] = clk.summary()
+        except Exception as e:
             out[name] = {"error": f"{type(e).__name__}: {e}"}
         out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
     return out

@@ -178,7 +178,7 @@ typedef struct {
                               candidate I gets K(I) = kmin + ceil((K - kmin) wref / (wref + W(I)))
                               iterations, W(I) = sum over v in I of 2 c4(v) + c6(v), c4 / c6 the 4- and
                               6-cycles through v (Sec. III, Table V) */
-    int32_t budget_kmin;   /* the smallest budget (1 <= kmin <= K) */
+    int32_t budget_kmin;   /* the smallest budget (1 <= kmin <= K; K <= 65535 with a budget) */
 } tsx_enum_params;
 
 /* Fills `p` with the defaults: NMS int16, K=20, base 16, sat 511, alpha 3/4,
@@ -348,6 +348,82 @@ TSX_API void is_params_default(tsx_is_params *p);
  * bounds), TSX_ENOMEM, TSX_ECUDA. */
 TSX_API int is_fer_estimate(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_is_params *params,
                             void *stream, tsx_is_result *out, uint8_t *fail_out, double *logw_out);
+
+/* ---- the simulation decoder (Sec. III, the FER curves of Fig. 2) -------
+ * Quantized normalized layered min-sum: LLR, check-to-variable and
+ * variable-to-check widths of 4, 4 and 6 bits, 20 iterations.  Readings (the
+ * paper names the widths only): a w-bit value saturates to
+ * +-(2^(w-1) - 1); a layer is a row block of the QC base matrix; the
+ * posterior P_v starts at the saturated channel value and stays at the
+ * variable-to-check width; per layer and check q = sat_v2c(P_v - r),
+ * r = sign * sat_c2v((alpha_num m) >> alpha_shift) with m the smallest |q| of
+ * the other edges (sgn 0 = +1; a check of degree 1 sends sat_c2v), then
+ * P_v = sat_v2c(q + r); x = [P < 0] and the syndrome are checked before the
+ * first iteration and after each.  Failure: x != 0.  QC codes only
+ * (TSX_EUNSUPPORTED otherwise). */
+typedef struct {
+    int32_t K;                              /* iterations (20) */
+    int32_t llr_bits, c2v_bits, v2c_bits;   /* 4, 4, 6 (each 2..8) */
+    int32_t alpha_num, alpha_shift;         /* 3, 2 */
+} tsx_lnms_params;
+TSX_API void lnms_params_default(tsx_lnms_params *p);
+
+/* Decodes n_frames frames of channel values.  All pointers are device
+ * memory: llr [n_frames][n] int8 (saturated to the LLR width here), fail
+ * [n_frames] bytes out (1 = x != 0), iters [n_frames] out (may be NULL), x
+ * [n_frames][n] bytes out (the decision, may be NULL).  Enqueued on `stream`,
+ * not waited for.  Errors: TSX_EINVAL, TSX_EUNSUPPORTED, TSX_ENOMEM,
+ * TSX_ECUDA. */
+TSX_API int lnms_decode(tsx_code *code, const tsx_lnms_params *p, const int8_t *llr, int64_t n_frames,
+                        uint8_t *fail, int32_t *iters, uint8_t *x, void *stream);
+
+/* Frame-error simulation with that decoder, the way the paper's curves were
+ * made (until a number of frame errors): BPSK of the all-zero word over
+ * AWGN, sigma^2 = 1 / (2 R Eb/N0); the noise of frame f is the
+ * importance-sampling generator's with key job_key and sample
+ * frame_begin + f (mu = 0); channel value round-half-away(2 y / sigma^2 *
+ * llr_scale) saturated to the LLR width.  Frames are decoded in chunks and
+ * counted in order: the run stops at the first frame count whose errors
+ * reach max_errors (0 = every frame), or at max_frames.  fail_out: host,
+ * max_frames bytes or NULL.  Synchronizes `stream`.  Errors as for
+ * lnms_decode(). */
+typedef struct {
+    double ebn0_db;
+    double rate;        /* 0 = 1 - m/n */
+    double llr_scale;   /* LLR quantization step is 1 / llr_scale (1.0) */
+    int64_t max_frames;
+    int64_t max_errors; /* 200 */
+    uint64_t job_key;
+    int64_t frame_begin;
+} tsx_sim_params;
+typedef struct {
+    int64_t frames, frame_errors, bit_errors;
+    double fer, ber;    /* frame_errors / frames, bit_errors / (frames n) */
+    int64_t iterations, edge_updates;
+    double ms;          /* device time of the decode launches (CUDA events) */
+} tsx_sim_result;
+TSX_API void sim_params_default(tsx_sim_params *p);
+TSX_API int lnms_simulate(tsx_code *code, const tsx_lnms_params *p, const tsx_sim_params *sp, void *stream,
+                          tsx_sim_result *out, uint8_t *fail_out);
+
+/* ---- the generalized union bound (Sec. II-III) --------------------------
+ * The error-floor estimate the paper builds from the trapping-set list with
+ * Cole's weighting: FER_UB = sum over the sets of mult_i * FER_i, FER_i the
+ * importance-sampling estimate of is_fer_estimate() toward set i with job key
+ * params->job_key + i, and its variance sum mult_i^2 var_i.  ts_vars: host,
+ * the sets' variable nodes one after the other, set i at
+ * ts_vars[ts_off[i] .. ts_off[i+1]); mult: host, n_sets multiplicities (the
+ * orbit sizes of a QC list, 1 for a general code); fer_out: host, n_sets
+ * per-set estimates or NULL.  The sets' sampling launches are enqueued on
+ * `stream` together and waited for once.  Errors as for is_fer_estimate(). */
+typedef struct {
+    double fer_ub, var_ub;
+    int64_t n_sets, samples, n_fail, edge_updates;
+    double ms;          /* device time from the first launch to the last (CUDA events) */
+} tsx_union_result;
+TSX_API int union_bound_fer(tsx_code *code, int64_t n_sets, const int32_t *ts_vars, const int64_t *ts_off,
+                            const double *mult, const tsx_is_params *params, void *stream, tsx_union_result *out,
+                            double *fer_out);
 
 /* ---- serving runtime (no counterpart in the paper) --------------------
  * A request loop over resident codes: enumeration and importance-sampling

@@ -130,6 +130,8 @@ def lib():
             L.og_normals4.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, F32P]
             L.og_is_samples.argtypes = [C.c_void_p, I32P, C.c_int, C.POINTER(_IsParams), C.c_uint64, C.c_int,
                                         U8P, F64P]
+            L.og_lnms_frames.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_uint64, C.c_uint64, C.c_int,
+                                         C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, U8P, I32P, I32P]
             L.og_is_quant.argtypes = [C.c_float, C.c_float, C.c_int]
             L.og_is_quant.restype = C.c_int
             L.og_is_channel.argtypes = [C.c_void_p, I32P, C.c_int, C.POINTER(_IsParams), C.c_uint64, I32P, F32P]
@@ -292,6 +294,18 @@ class Graph:
         f = lib().og_decode_lnms(self.h, Lv, K, llr_bits, c2v_bits, v2c_bits, alpha_num, alpha_shift, x,
                                  C.byref(kl))
         return bool(f), x, kl.value
+
+    def lnms_frames(self, *, ebn0_db, rate=None, llr_scale=1.0, job=0, f0=0, n=100, K=20, llr_bits=4, c2v_bits=4,
+                    v2c_bits=6, alpha_num=3, alpha_shift=2):
+        """Frames of the layered decoder's frame-error simulation: per frame the
+        failure flag, iterations and the Hamming weight of the decision."""
+        r = (1.0 - self.m / self.n) if rate is None else rate
+        fail = np.zeros(n, dtype=np.uint8)
+        it = np.zeros(n, dtype=np.int32)
+        w = np.zeros(n, dtype=np.int32)
+        lib().og_lnms_frames(self.h, float(ebn0_db), float(r), float(llr_scale), int(job), int(f0), int(n), K,
+                             llr_bits, c2v_bits, v2c_bits, alpha_num, alpha_shift, fail, it, w)
+        return fail, it, w
 
     def decode_spa(self, Lv, K, clip=30.0, wstart=None, libm=False):
         Lv = np.ascontiguousarray(np.asarray(Lv, dtype=np.float32))

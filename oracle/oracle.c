@@ -1328,3 +1328,40 @@ void og_is_samples(const og_graph *g, const int *T, int a, const og_is_params *p
     }
     free(L); free(inT); free(xb); free(nv);
 }
+
+/* ------------------------------------------------------------------ */
+/* Frame-error simulation with the layered decoder (Fig. 2 setup)      */
+/* ------------------------------------------------------------------ */
+/* Frames f0 .. f0 + nf - 1: BPSK of the all-zero word over AWGN with
+ * sigma^2 = 1 / (2 R Eb/N0), the noise of frame f the importance-sampling
+ * generator's with key job and sample f (no shift); channel value
+ * round-half-away(y * cq) with cq = 2 llr_scale / sigma^2 (single
+ * precision), saturated to the LLR width; decoded by og_decode_lnms.  Per
+ * frame: fail (x != 0), iterations, Hamming weight of x. */
+void og_lnms_frames(const og_graph *g, double ebn0_db, double rate, double llr_scale, uint64_t job, uint64_t f0,
+                    int nf, int K, int llr_bits, int c2v_bits, int v2c_bits, int an, int as, unsigned char *fail,
+                    int *iters, int *weight) {
+    double s2 = 1.0 / (2.0 * rate * pow(10.0, ebn0_db / 10.0));
+    float sigf = (float)sqrt(s2), cq = (float)(2.0 * llr_scale / s2);
+    int lim = (1 << (llr_bits - 1)) - 1;
+    int *L = (int *)malloc(sizeof(int) * g->n);
+    unsigned char *x = (unsigned char *)malloc(g->n);
+    for (int i = 0; i < nf; i++) {
+        for (int q = 0; 4 * q < g->n; q++) {
+            float gq[4];
+            og_normals4(job, f0 + (uint64_t)i, (uint32_t)q, gq);
+            for (int j = 0; j < 4 && 4 * q + j < g->n; j++) {
+                float y = 1.0f + sigf * gq[j];
+                L[4 * q + j] = og_is_quant(y, cq, lim);
+            }
+        }
+        int kl;
+        fail[i] = (unsigned char)og_decode_lnms(g, L, K, llr_bits, c2v_bits, v2c_bits, an, as, x, &kl);
+        iters[i] = kl;
+        int w = 0;
+        for (int v = 0; v < g->n; v++) w += x[v];
+        weight[i] = w;
+    }
+    free(L);
+    free(x);
+}

@@ -27,6 +27,9 @@ from ._tsx import (  # noqa: F401
     is_fer_estimate,
     is_params_default,
     lib,
+    lnms_decode,
+    lnms_params,
+    lnms_simulate,
     load_code,
     make_params,
     measure_peaks,
@@ -35,4 +38,5 @@ from ._tsx import (  # noqa: F401
     ts_list_stats,
     ts_list_view,
     tune_tile,
+    union_bound_fer,
 )

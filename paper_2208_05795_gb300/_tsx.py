@@ -107,6 +107,26 @@ class Peaks(C.Structure):
                 ("fp32_fma_per_clk_sm", C.c_double)]
 
 
+class LnmsParams(C.Structure):
+    _fields_ = [("K", C.c_int32), ("llr_bits", C.c_int32), ("c2v_bits", C.c_int32), ("v2c_bits", C.c_int32),
+                ("alpha_num", C.c_int32), ("alpha_shift", C.c_int32)]
+
+
+class SimParams(C.Structure):
+    _fields_ = [("ebn0_db", C.c_double), ("rate", C.c_double), ("llr_scale", C.c_double), ("max_frames", C.c_int64),
+                ("max_errors", C.c_int64), ("job_key", C.c_uint64), ("frame_begin", C.c_int64)]
+
+
+class SimResult(C.Structure):
+    _fields_ = [("frames", C.c_int64), ("frame_errors", C.c_int64), ("bit_errors", C.c_int64), ("fer", C.c_double),
+                ("ber", C.c_double), ("iterations", C.c_int64), ("edge_updates", C.c_int64), ("ms", C.c_double)]
+
+
+class UnionResult(C.Structure):
+    _fields_ = [("fer_ub", C.c_double), ("var_ub", C.c_double), ("n_sets", C.c_int64), ("samples", C.c_int64),
+                ("n_fail", C.c_int64), ("edge_updates", C.c_int64), ("ms", C.c_double)]
+
+
 class EmdSpectrum(C.Structure):
     _fields_ = [("lmax", C.c_int32), ("walks", C.c_int64 * 7), ("count2l", (C.c_int64 * 128) * 7), ("ms", C.c_double)]
 
@@ -204,6 +224,17 @@ def lib():
             L.cycle_counts.restype = C.c_int
             L.emd_spectrum.argtypes = [vp, C.c_int32, vp, C.POINTER(EmdSpectrum)]
             L.emd_spectrum.restype = C.c_int
+            L.lnms_params_default.argtypes = [C.POINTER(LnmsParams)]
+            L.lnms_params_default.restype = None
+            L.sim_params_default.argtypes = [C.POINTER(SimParams)]
+            L.sim_params_default.restype = None
+            L.lnms_decode.argtypes = [vp, C.POINTER(LnmsParams), vp, C.c_int64, vp, vp, vp, vp]
+            L.lnms_decode.restype = C.c_int
+            L.lnms_simulate.argtypes = [vp, C.POINTER(LnmsParams), C.POINTER(SimParams), vp, C.POINTER(SimResult), vp]
+            L.lnms_simulate.restype = C.c_int
+            L.union_bound_fer.argtypes = [vp, C.c_int64, vp, vp, vp, C.POINTER(IsParams), vp, C.POINTER(UnionResult),
+                                          vp]
+            L.union_bound_fer.restype = C.c_int
             L.measure_peaks.argtypes = [C.POINTER(Peaks), vp]
             L.measure_peaks.restype = C.c_int
             _lib = L
@@ -626,3 +657,71 @@ def emd_spectrum(code: Code, lmax: int, stream=None) -> dict:
     walks = np.array(out.walks[:], dtype=np.int64)
     count2l = np.array([row[:] for row in out.count2l], dtype=np.int64)
     return {"lmax": int(out.lmax), "walks": walks, "count2l": count2l, "ms": float(out.ms)}
+
+
+def lnms_params(**kw) -> LnmsParams:
+    p = LnmsParams()
+    lib().lnms_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def lnms_decode(code: Code, llr_ptr: int, n_frames: int, fail_ptr: int, iters_ptr=None, x_ptr=None, stream=None,
+                **kw) -> None:
+    """lnms_decode(): the layered simulation decoder on caller frames; every
+    pointer is a device address (int) of the caller's buffers."""
+    p = lnms_params(**kw)
+    _check(lib().lnms_decode(code.h, C.byref(p), llr_ptr, int(n_frames), fail_ptr, iters_ptr, x_ptr,
+                             _stream_handle(stream)), "lnms_decode")
+
+
+def lnms_simulate(code: Code, stream=None, record: bool = False, **kw) -> dict:
+    """lnms_simulate(): frame-error simulation with the layered decoder.
+    Keyword arguments set tsx_lnms_params and tsx_sim_params fields; with
+    record, the per-frame failure flags are returned as well."""
+    lp = LnmsParams()
+    lib().lnms_params_default(C.byref(lp))
+    sp = SimParams()
+    lib().sim_params_default(C.byref(sp))
+    for k, v in kw.items():
+        if hasattr(lp, k):
+            setattr(lp, k, v)
+        elif hasattr(sp, k):
+            setattr(sp, k, v)
+        else:
+            raise TypeError(f"unknown parameter {k}")
+    r = SimResult()
+    fail = np.zeros(int(sp.max_frames), dtype=np.uint8) if record else None
+    _check(lib().lnms_simulate(code.h, C.byref(lp), C.byref(sp), _stream_handle(stream), C.byref(r),
+                               fail.ctypes.data_as(C.c_void_p) if record else None), "lnms_simulate")
+    out = {k: getattr(r, k) for k, _ in SimResult._fields_}
+    if record:
+        out["fail"] = fail[:int(r.frames)]
+    return out
+
+
+def union_bound_fer(code: Code, sets, mult, stream=None, **kw) -> dict:
+    """union_bound_fer(): sum over the sets of mult * the importance-sampling
+    FER toward the set (job key job_key + i for set i); keyword arguments set
+    tsx_is_params fields."""
+    p = is_params_default()
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    sets = [np.asarray(t, dtype=np.int32) for t in sets]
+    off = np.zeros(len(sets) + 1, dtype=np.int64)
+    off[1:] = np.cumsum([len(t) for t in sets])
+    flat = np.ascontiguousarray(np.concatenate(sets) if sets else np.zeros(0, np.int32), dtype=np.int32)
+    m = np.ascontiguousarray(np.asarray(mult, dtype=np.float64))
+    fer = np.zeros(len(sets), dtype=np.float64)
+    r = UnionResult()
+    _check(lib().union_bound_fer(code.h, len(sets), flat.ctypes.data_as(C.c_void_p), off.ctypes.data_as(C.c_void_p),
+                                 m.ctypes.data_as(C.c_void_p), C.byref(p), _stream_handle(stream), C.byref(r),
+                                 fer.ctypes.data_as(C.c_void_p)), "union_bound_fer")
+    out = {k: getattr(r, k) for k, _ in UnionResult._fields_}
+    out["fer"] = fer
+    return out

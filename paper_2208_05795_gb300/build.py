@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtsx.so")
 SOURCES = ["api.cu", "cand.cu", "decode.cu", "decode_i16.cu", "decode_i8.cu", "decode_spa.cu", "sieve.cu", "noalloc.cu", "isfer.cu",
-           "server.cu", "peaks.cu", "list.cu", "cycles.cu"]
+           "server.cu", "peaks.cu", "list.cu", "cycles.cu", "lnms.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

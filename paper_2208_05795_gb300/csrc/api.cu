@@ -58,6 +58,7 @@ struct tsx_ts_list {
     // decode launch shape: one launch over the whole range (dchunk = 0) or
     // one launch per dchunk candidates, each with its own queue word
     long long dchunk = 0, n_dchunks = 0, range_end = 0;
+    long long cand_bound = 0;
     unsigned long long *d_queues = nullptr;
     int grid_sms = 0;
     // sizing only: allocations are counted, not made
@@ -502,7 +503,7 @@ static int check_params(const tsx_enum_params &p) {
     if (p.list_mode && p.decoder == TSX_DEC_SPA_F32) return TSX_EUNSUPPORTED;
     if (p.list_mode && p.K > 1000) return TSX_EUNSUPPORTED;
     if (p.budget_wref < 0) return TSX_EINVAL;
-    if (p.budget_wref > 0 && (p.budget_kmin < 1 || p.budget_kmin > p.K)) return TSX_EINVAL;
+    if (p.budget_wref > 0 && (p.budget_kmin < 1 || p.budget_kmin > p.K || p.K > 65535)) return TSX_EINVAL;
     return TSX_OK;
 }
 
@@ -517,7 +518,6 @@ int enum_params_to_decode(const tsx_enum_params *p, DecodeParams *dp) {
     dp->decoder = p->decoder; dp->K = p->K; dp->base_llr = p->base_llr; dp->sat = p->sat;
     dp->alpha_num = p->alpha_num; dp->alpha_shift = p->alpha_shift; dp->amp_steps = p->amp_steps;
     dp->spa_clip = p->spa_clip; dp->spa_amax = p->spa_amax;
-    dp->budget_wref = 0; dp->budget_kmin = 0; dp->vweight = nullptr;
     return TSX_OK;
 }
 }  // namespace tsx
@@ -615,22 +615,28 @@ static int prepare_list(tsx_code *code, const tsx_enum_params *params, cudaStrea
     L->cycles = cycles;
     L->cyc_l = l;
     L->paths = paths;
-    // list mode: several sets per failing candidate
-    L->cap = next_pow2(std::max<long long>(1024, (p.list_mode ? 4 : 2) * std::max<long long>(n_rec, 1)));
-    L->pool_cap = std::max<long long>(1 << 20, (p.list_mode ? 48 : 24) * n_rec);
+    // list mode: up to two sets per iteration of every failing candidate
+    if (p.list_mode) {
+        const long long want = std::max<long long>(1, n_rec) * (long long)(p.K + 1);
+        L->cap = next_pow2(std::min<long long>(std::max<long long>(1 << 16, want), 1LL << 28));
+        L->pool_cap = std::min<long long>(L->cap * 24, 0xfffffff0LL);
+    } else {
+        L->cap = next_pow2(std::max<long long>(1024, 2 * std::max<long long>(n_rec, 1)));
+        L->pool_cap = std::max<long long>(1 << 20, 24 * n_rec);
+    }
     if (L->pool_cap > 0xfffffff0LL) L->pool_cap = 0xfffffff0LL;
     DecodeParams &dp = L->dp;
     dp.decoder = p.decoder; dp.K = p.K; dp.base_llr = p.base_llr; dp.sat = p.sat;
     dp.alpha_num = p.alpha_num; dp.alpha_shift = p.alpha_shift; dp.amp_steps = p.amp_steps;
     dp.spa_clip = p.spa_clip; dp.spa_amax = p.spa_amax;
-    dp.budget_wref = p.budget_wref; dp.budget_kmin = p.budget_kmin;
-    dp.vweight = p.budget_wref > 0 ? code->vweight : nullptr;
 
     L->n_chunks = cand_chunks(raw_total);
     L->d_raw_off = lalloc<long long>(L, n_rep + 1, s);
     L->d_chunk_cnt = lalloc<int>(L, L->n_chunks, s);
     L->d_chunk_off = lalloc<long long>(L, L->n_chunks + 1, s);
     int4 *d_cands = lalloc<int4>(L, cand_bound, s);
+    L->b.cand_K = p.budget_wref > 0 ? lalloc<uint16_t>(L, cand_bound, s) : nullptr;
+    L->cand_bound = cand_bound;
     L->d_cyc_cnt = cycles ? lalloc<int>(L, n_rep, s) : nullptr;
     L->d_cyc_off = cycles ? lalloc<long long>(L, n_rep + 1, s) : nullptr;
     EnumBuffers &b = L->b;
@@ -732,6 +738,9 @@ static int enqueue_front(tsx_ts_list *L, cudaStream_t s) {
             launch_cand_cycle(cy, true, s) != cudaSuccess)
             return TSX_ECUDA;
     }
+    if (L->b.cand_K && launch_budget(b.cands, L->cand_bound, L->code->vweight, L->p.K, L->p.budget_kmin,
+                                     L->p.budget_wref, (uint16_t *)L->b.cand_K, L->ctr, s) != cudaSuccess)
+        return TSX_ECUDA;
     return record(L, 1, s);
 }
 

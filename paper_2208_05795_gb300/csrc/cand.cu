@@ -493,3 +493,37 @@ cudaError_t launch_cand_cycle(const CycleArgs &a, bool write, cudaStream_t st) {
 }
 
 }  // namespace tsx
+
+namespace tsx {
+
+// ------------------------------------------------------------------------
+// cycle-density iteration budgets (Sec. III: fewer iterations where short
+// cycles are dense): K(I) = kmin + ceil((K - kmin) wref / (wref + W(I))),
+// W(I) = sum over v in I of vweight[v] = 2 c4(v) + c6(v)
+// ------------------------------------------------------------------------
+__global__ void budget_kernel(const int4 *cands, long long bound, const int *vweight, int K, int kmin, int wref,
+                              uint16_t *cand_K, const Counters *ctr) {
+    const long long total = (long long)ctr->n_cand_total;
+    const long long n = total < bound ? total : bound;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int4 c = cands[i];
+        long long W = 0;
+        if (c.x >= 0) W += vweight[c.x];
+        if (c.y >= 0) W += vweight[c.y];
+        if (c.z >= 0) W += vweight[c.z];
+        if (c.w >= 0) W += vweight[c.w];
+        const long long den = (long long)wref + W;
+        cand_K[i] = (uint16_t)(kmin + (((long long)(K - kmin) * wref + den - 1) / den));
+    }
+}
+
+cudaError_t launch_budget(const int4 *cands, long long bound, const int *vweight, int K, int kmin, int wref,
+                          uint16_t *cand_K, const Counters *ctr, cudaStream_t st) {
+    long long blocks = (bound + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (blocks < 1) blocks = 1;
+    budget_kernel<<<(int)blocks, 256, 0, st>>>(cands, bound, vweight, K, kmin, wref, cand_K, ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace tsx

@@ -248,6 +248,8 @@ struct Misc {
     int red[16];
     long long bcast[2];
     int ints[8];
+    unsigned long long okd, okit;  // converged decodes of this group and their iterations
+    int K[2];                      // iteration limit of each half's candidate (two-codeword kernels)
     uint16_t seg[kMaxNb + 2];
 };
 
@@ -457,14 +459,9 @@ struct Decoder {
     }
 };
 
-// Iteration limit of candidate I: K, or with a cycle-density budget
-// kmin + ceil((K - kmin) wref / (wref + W(I))), W(I) = sum of vweight over I.
-__device__ __forceinline__ int cand_budget(const DecodeParams &dp, const int *I, int nI) {
-    if (dp.budget_wref <= 0) return dp.K;
-    long long W = 0;
-    for (int t = 0; t < nI; t++) W += dp.vweight[I[t]];
-    const long long den = (long long)dp.budget_wref + W;
-    return dp.budget_kmin + (int)(((long long)(dp.K - dp.budget_kmin) * dp.budget_wref + den - 1) / den);
+// Iteration limit of candidate idx: K, or its cycle-density budget.
+__device__ __forceinline__ int cand_limit(const DecodeParams &dp, const EnumBuffers &b, long long idx) {
+    return b.cand_K ? (int)b.cand_K[idx] : dp.K;
 }
 
 // ---------------------------------------------------------------------------
@@ -864,7 +861,7 @@ __device__ __forceinline__ void scalar_run(const DevCode &g, const DecodeParams 
         bool failed = false;
         int thr = -1;
         float thr_f = -1.0f;
-        const int Kc = cand_budget(dp, I, nI);
+        const int Kc = cand_limit(dp, b, idx);
         if constexpr (!Dec::kFloat) {
             int lo = 0, hi = (1 << dp.amp_steps) - 1;
             bool f = dec.run(I, nI, Lbase, (lv)clampi(dp.base_llr - hi, -dp.sat, dp.sat), xcur, kl, Kc);

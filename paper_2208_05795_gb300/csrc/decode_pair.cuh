@@ -77,7 +77,6 @@ struct Half {
     int failed;
     int Limp;  // channel LLR of the impulse nodes in the current decode
     int k, ubest;
-    int K;      // iteration limit of the candidate
     int first;  // current decode has run no check pass yet
     int cur;    // x buffer of the current decode (0/1); keep = cur ^ 1
     __device__ __forceinline__ int Ik(int t) const { return t == 0 ? I0 : t == 1 ? I1 : t == 2 ? I2 : I3; }
@@ -533,12 +532,18 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
     const int Lb = clampi(dp.base_llr, -dp.sat, dp.sat);
     const int amax = (1 << dp.amp_steps) - 1;
-    long long my_dec = 0, my_it = 0, my_ok = 0, my_okit = 0;
+    long long my_dec = 0, my_it = 0;
     int pcur = 0;  // which posterior buffer holds P_k
+    // the converged-decode counts and each half's iteration limit live in the
+    // group's shared misc area (written by thread 0 only), not in registers
+    if (gp.gt == 0) {
+        misc->okd = 0;
+        misc->okit = 0;
+    }
 
     Half H[2];
 
-    auto fetch = [&](Half &h) {
+    auto fetch = [&](Half &h, int hh) {
         if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(b.queue, 1ull);
         gp.sync();
         const long long idx = b.cand_begin + misc->bcast[0];
@@ -547,7 +552,6 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         h.ubest = 0x7fffffff;
         h.first = 1;
         h.cur = 0;
-        h.K = dp.K;
         if (idx >= end) {
             h.idx = -1;
             h.nI = 0;
@@ -560,12 +564,8 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         h.lo = 0; h.hi = amax; h.st = 0; h.phase = 0;
         h.thr = -1; h.ndec = 0; h.nit = 0; h.failed = 0;
         h.Limp = clampi(dp.base_llr - amax, -dp.sat, dp.sat);
-        if (dp.budget_wref > 0) {
-            const int Iv[4] = {h.I0, h.I1, h.I2, h.I3};
-            h.K = cand_budget(dp, Iv, h.nI);
-        } else {
-            h.K = dp.K;
-        }
+        if (gp.gt == 0) misc->K[hh] = cand_limit(dp, b, idx);
+        // (read after the next group barrier)
     };
     // finish the candidate of half hh (records, x* to global) and fetch the next
     auto finish = [&](Half &h, int hh) {
@@ -586,7 +586,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         }
         my_dec += h.ndec;
         my_it += h.nit;
-        fetch(h);
+        fetch(h, hh);
     };
     // Advance half hh past trivial decodes (impulse LLR >= 0: every hard
     // decision 0, u_0 = 0, success at iteration 0) until a decode that needs
@@ -595,7 +595,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         while (h.idx >= 0) {
             if (h.Limp < 0) return true;
             h.ndec++;
-            my_ok++;  // x_0 = 0: converged at iteration 0
+            if (gp.gt == 0) misc->okd++;  // x_0 = 0: converged at iteration 0
             if (h.phase == 0) {
                 finish(h, hh);  // no failure at the largest amplitude
                 continue;
@@ -642,7 +642,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         unsigned *Pc = Pbuf, *Pn = Pbuf + g.n;
         if constexpr (!VN) dec.init_accum(Pn, Lb);
         for (int hh = 0; hh < 2; hh++) {
-            fetch(H[hh]);
+            fetch(H[hh], hh);
             settle(H[hh], hh);
             start_cur(H[hh], hh, Pc);  // idle halves too: every word stays a valid decode state
         }
@@ -658,7 +658,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         unsigned *Pc = VN ? Pbuf : Pbuf + pcur * g.n, *Pn = VN ? Pbuf : Pbuf + (pcur ^ 1) * g.n;
         const unsigned km = (H[0].first ? 0xFFFF0000u : 0xFFFFFFFFu) & (H[1].first ? 0x0000FFFFu : 0xFFFFFFFFu);
         const unsigned kb = pc.B2 & ~km;
-        const bool wr = (H[0].idx >= 0 && H[0].k < H[0].K) || (H[1].idx >= 0 && H[1].k < H[1].K);
+        const bool wr = (H[0].idx >= 0 && H[0].k < misc->K[0]) || (H[1].idx >= 0 && H[1].k < misc->K[1]);
         // u_k of both halves from P_k = Pc; Pn accumulates P_{k+1}
         const int us = km != 0xFFFFFFFFu ? dec.template check_pass<true>(km, kb, wr, Pc, Pn)
                                          : dec.template check_pass<false>(km, kb, wr, Pc, Pn);
@@ -672,16 +672,16 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
                 h.ubest = u;
                 dec.save_x(Pc, hh, xc);
             }
-            if (u != 0 && h.k != h.K) continue;
+            if (u != 0 && h.k != misc->K[hh]) continue;
             // the decode ended at K_last = k
             const int kl = h.k;
             if (kl < g.wstart) dec.save_x(Pc, hh, xc);
             const bool fail = u != 0 || dec.any_neg(Pc, hh) != 0;
             h.ndec++;
             h.nit += kl;
-            if (!fail) {
-                my_ok++;
-                my_okit += kl;
+            if (!fail && gp.gt == 0) {
+                misc->okd++;
+                misc->okit += kl;
             }
             if (h.phase == 0) {
                 if (!fail) {
@@ -754,8 +754,8 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         atomicAdd(&b.ctr->decodes, (unsigned long long)my_dec);
         atomicAdd(&b.ctr->iterations, (unsigned long long)my_it);
         atomicAdd(&b.ctr->edge_updates, (unsigned long long)my_it * (unsigned long long)g.E);
-        atomicAdd(&b.ctr->ok_decodes, (unsigned long long)my_ok);
-        atomicAdd(&b.ctr->ok_iters, (unsigned long long)my_okit);
+        atomicAdd(&b.ctr->ok_decodes, misc->okd);
+        atomicAdd(&b.ctr->ok_iters, misc->okit);
     }
 }
 

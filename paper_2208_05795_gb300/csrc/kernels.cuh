@@ -35,6 +35,10 @@ cudaError_t launch_cand_cycle(const CycleArgs &a, bool write, cudaStream_t st);
 cudaError_t launch_scan(const int *cnt, long long n, long long *off, const long long *base, Counters *ctr,
                         bool add_total, cudaStream_t st);
 long long cand_chunks(long long raw_total);
+// Per-candidate iteration limits of the cycle-density budget for the first
+// min(bound, candidate count) candidates.
+cudaError_t launch_budget(const int4 *cands, long long bound, const int *vweight, int K, int kmin, int wref,
+                          uint16_t *cand_K, const Counters *ctr, cudaStream_t st);
 
 // ---- impulse decoding, bisection, extraction, dedupe (decode.cu) --------
 struct SlotLayout {

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(512) list_kernel(DevCode g, DecodeParams dp, E
         const int I[4] = {I4.x, I4.y, I4.z, I4.w};
         const int nI = (I4.x >= 0) + (I4.y >= 0) + (I4.z >= 0) + (I4.w >= 0);
         const int Limp = clampi(dp.base_llr - thr, -dp.sat, dp.sat);
-        const int Kc = cand_budget(dp, I, nI);
+        const int Kc = cand_limit(dp, b, b.cand_begin + o);
         if (gp.gt == 0) misc->ints[0] = 0;  // sets this candidate has counted
         for (int v = gp.gt; v < g.n; v += gp.T) P[v] = (int16_t)Lbase;
         gp.sync();

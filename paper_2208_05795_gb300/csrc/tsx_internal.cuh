@@ -90,11 +90,6 @@ constexpr int kPoolHdr = 4;
 struct DecodeParams {
     int decoder;  // TSX_DEC_*
     int K;
-    // cycle-density iteration budget: wref > 0 gives candidate I
-    // kmin + ceil((K - kmin) wref / (wref + W(I))) iterations, W(I) the sum of
-    // vweight over I
-    int budget_wref, budget_kmin;
-    const int *vweight;  // [n] 2 c4(v) + c6(v) (device), with wref > 0
     int base_llr;
     int sat;
     int alpha_num, alpha_shift;
@@ -120,6 +115,9 @@ struct EnumBuffers {
     int *c_flags;
     int *c_decodes;
     int *c_iters;
+    // per-candidate iteration limits (indexed like cands), or null: every
+    // candidate gets K (the cycle-density budgets of budget_kernel)
+    const uint16_t *cand_K;
     // best error pattern x* of every failing candidate, nw words each
     uint32_t *xstar;
     int nw;

@@ -18,7 +18,12 @@ Workloads:
             every other member (general codes have no automorphism, so
             every variable node is a representative).
 
-  python tests/golden/make_spectra.py [qc2640|peg1008_shard ...] [--procs N]
+  code1_emd -- the EMD spectrum of Code 1 (Table V) up to 12-cycles: per
+            cycle length 2l and EMD e, the oracle's class-weighted count
+            (count2l; count2l / 2l cycles per circulant orbit), from the 20
+            representatives (j, 0) (written to emd_code1_l6.txt).
+
+  python tests/golden/make_spectra.py [qc2640|peg1008_shard|code1_emd ...] [--procs N]
 """
 from __future__ import annotations
 
@@ -126,13 +131,50 @@ def spectrum(name, procs):
     print(f"{name}: {n} candidates, {len(order)} trapping sets, {time.time() - t0:.0f} s -> {out}", flush=True)
 
 
+def _walks_job(args):
+    code, v, lmax = args
+    return oracle.Graph(code).cycle_walks(v, lmax, emd=True)
+
+
+def code1_emd(procs, lmax=6):
+    t0 = time.time()
+    rows, Z = [], None
+    with open(os.path.join(HERE, "code1_table5.txt")) as f:
+        for line in f:
+            tok = line.split("#", 1)[0].split()
+            if tok and tok[0] == "Z":
+                Z = int(tok[1])
+            elif tok and tok[0][0] in "-0123456789":
+                rows.append([int(x) for x in tok])
+    code = synth.qc_code(np.array(rows, dtype=np.int32), Z)
+    with mp.get_context("spawn").Pool(procs) as pool:
+        parts = pool.map(_walks_job, [(code, j * Z, lmax) for j in range(len(rows[0]))], chunksize=1)
+    hist = sum(p[1] for p in parts)
+    walks = sum(p[0] for p in parts)
+    out = os.path.join(HERE, "emd_code1_l6.txt")
+    with open(out, "w") as f:
+        f.write("# The oracle's EMD spectrum of Code 1 (Table V), written by make_spectra.py code1_emd:\n"
+                "# closed exponent chains (Prop. 1) of l = 2..6 variable nodes from the representatives (j, 0);\n"
+                "# count2l / (2 l) is the number of cycles of length 2l and EMD e per circulant orbit.\n"
+                "# l emd count2l   (and: walks l total)\n")
+        for l in range(2, lmax + 1):
+            f.write(f"walks {l} {int(walks[l])}\n")
+            for e in np.flatnonzero(hist[l]):
+                f.write(f"{l} {int(e)} {int(hist[l, e])}\n")
+    print(f"code1_emd: {time.time() - t0:.0f} s -> {out}", flush=True)
+
+
 def main():
-    names = [a for a in sys.argv[1:] if not a.startswith("--")] or ["qc2640", "peg1008_shard"]
+    names = [a for a in sys.argv[1:] if not a.startswith("--") and not a.isdigit()] or \
+        ["qc2640", "peg1008_shard", "code1_emd"]
     procs = os.cpu_count() or 1
     if "--procs" in sys.argv:
         procs = int(sys.argv[sys.argv.index("--procs") + 1])
     for name in names:
-        spectrum(name, procs)
+        if name == "code1_emd":
+            code1_emd(procs)
+        else:
+            spectrum(name, procs)
 
 
 if __name__ == "__main__":

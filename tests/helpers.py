@@ -106,3 +106,15 @@ def emd(cn_sets, H, vs):
     """Extrinsic message degree: checks adjacent to exactly one VN of the set."""
     cnt = H[:, sorted(vs)].sum(axis=1)
     return int((cnt == 1).sum())
+
+
+def load_emd_golden(name="emd_code1_l6.txt"):
+    """The oracle's EMD spectrum file (make_spectra.py code1_emd): walks[l] and count2l[l, e]."""
+    walks = np.zeros(7, dtype=np.int64)
+    hist = np.zeros((7, 128), dtype=np.int64)
+    for tok in _rows(name):
+        if tok[0] == "walks":
+            walks[int(tok[1])] = int(tok[2])
+        else:
+            hist[int(tok[0]), int(tok[1])] = int(tok[2])
+    return walks, hist

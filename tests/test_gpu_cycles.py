@@ -34,20 +34,24 @@ def test_code1_table2_up_to_12_cycles():
     code, _ = _code1()
     c = tsx.load_code(code)
     s = tsx.emd_spectrum(c, 6)
+    # the oracle, walk for walk (its 12-cycle search is written by make_spectra.py)
+    walks, hist = helpers.load_emd_golden()
+    assert np.array_equal(s["count2l"][:7], hist)
+    assert np.array_equal(s["walks"][2:7], walks[2:7])
+    # Table II: rows 4 to 10 in full (printed rounded: 5380.5 as 5381); row 12
+    # in full except EMD 2, 5 and 6, where closed chains made of two distinct
+    # shorter cycles sharing a path are counted here and not in the table
     want = helpers.load_table2_code1()
     for (clen, e), count in want.items():
         l = clen // 2
         got = s["count2l"][l, e] / (2 * l)
-        assert abs(got - count) <= 0.5 and round(got + 1e-9) in (count, count + 1) and \
-            (got == count or got == count - 0.5), (clen, e, got, count)
+        if clen == 12 and e in (2, 5, 6):
+            assert got > count, (clen, e, got, count)
+            continue
+        assert got == count or got == count - 0.5, (clen, e, got, count)
     for l in range(2, 7):
         for e in np.flatnonzero(s["count2l"][l]):
             assert (2 * l, int(e)) in want, (2 * l, e)
-    # the oracle, up to 10-cycles, walk for walk
-    walks, hist = _oracle_spectrum(code, 5, [j * code.Z for j in range(20)])
-    s5 = tsx.emd_spectrum(c, 5)
-    assert np.array_equal(s5["count2l"][:6], hist[:6])
-    assert np.array_equal(s5["walks"][:6], walks[:6])
 
 
 @pytest.mark.parametrize("name,lmax", [("qc96", 6), ("peg1008", 5), ("qc2640", 6)])

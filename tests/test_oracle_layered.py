@@ -74,3 +74,27 @@ def test_codeword_inputs_stop_at_once():
     L = np.array([-5, -5, -5, -5, 6, 6], np.int32)  # x = (1,1,1,1,0,0) satisfies every check
     f, x, kl = g.decode_lnms(L, K=20)
     assert f and kl == 0 and x.tolist() == [1, 1, 1, 1, 0, 0]
+
+
+def test_simulation_channel_from_the_definition():
+    # frame f: y = 1 + sigma g (g the importance-sampling generator's normals of
+    # sample f), channel value round-half-away(2 y / sigma^2 * scale) saturated to
+    # the LLR width; decoding those values gives the simulation's flags
+    import math
+    code = synth.workload("qc96")["code"]
+    g = oracle.Graph(code)
+    ebn0, scale, job = 2.0, 0.75, 9
+    R = 1.0 - g.m / g.n
+    s2 = 1.0 / (2.0 * R * 10 ** (ebn0 / 10))
+    sig, cq = np.float32(math.sqrt(s2)), np.float32(2.0 * scale / s2)
+    fail, it, w = g.lnms_frames(ebn0_db=ebn0, llr_scale=scale, job=job, f0=100, n=60)
+    n_sat = 0
+    for i in range(60):
+        gn = np.concatenate([oracle.normals4(job, 100 + i, q) for q in range((g.n + 3) // 4)])[:g.n].astype(np.float32)
+        y = (np.float32(1.0) + (sig * gn).astype(np.float32)).astype(np.float32)
+        prod = (y * cq).astype(np.float32).astype(np.float64)
+        L = np.clip(np.sign(prod) * np.floor(np.abs(prod) + 0.5), -7, 7).astype(np.int32)
+        n_sat += int((np.abs(L) == 7).sum())
+        f, x, kl = g.decode_lnms(L, K=20)
+        assert (bool(fail[i]), int(it[i]), int(w[i])) == (f, kl, int(x.sum())), i
+    assert n_sat > 0 and fail.any()
