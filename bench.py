@@ -101,6 +101,16 @@ def alu_roofline(eu_per_launch, ms_launch, pk, sm_mhz, packed=True, traffic=None
             "note": note or "peaks measured by measure_peaks() per SM clock, at the sampled median SM clock"}
 
 
+# the extra workloads, also runnable on their own (one JSON line each):
+# name -> (metric, unit, key of the value in the extra's summary)
+EXTRA_WORKLOADS = {
+    "list2640": ("ordered-list distinct trapping sets/s", "trapping sets/s", "distinct_ts_per_s"),
+    "budget_peg": ("iteration-budget speed-up over K for all", "x", "speedup"),
+    "lnms_code1": ("layered-decoder frames/s", "frames/s", "frames_per_s"),
+    "emd_code1": ("EMD spectrum search time", "ms", "ms"),
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -108,7 +118,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="peg1008",
-                    choices=sorted(synth.WORKLOADS) + ["batch32", "serve", "isfer"])
+                    choices=sorted(synth.WORKLOADS) + ["batch32", "serve", "isfer"] + sorted(EXTRA_WORKLOADS))
     ap.add_argument("--samples", type=int, default=1_000_000, help="isfer: samples per step")
     ap.add_argument("--no-graph", action="store_true", help="batch32: launch each step eagerly instead of "
                                                              "replaying the captured graph")
@@ -863,13 +873,15 @@ def _timed(fn, stream):
     return e0.elapsed_time(e1), out
 
 
-def extra_list(tsx, pk, stream, steps=2):
+def extra_list(tsx, pk, stream, steps=2, limit=-1):
     """The ordered list of Sec. III on the 2640-node QC code (every canonical
     candidate, K = 100): first stage (the enumeration decode) and second stage
     (replay and sieve of every x_k from ceil(average converged iterations))."""
     w = synth.workload("qc2640")
     c = tsx.load_code(w["code"], stream=stream)
     p = params_of(w, "nms16")
+    if limit >= 0:
+        p["cand_end"] = limit
     for _ in range(1):
         tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, list_mode=1, kstart=-1, **p))
     rows = []
@@ -997,11 +1009,35 @@ def run_extras(args, tsx, pk):
     return out
 
 
+def run_extra_alone(args):
+    import torch
+    import paper_2208_05795_gb300 as tsx
+    from paper_2208_05795_gb300 import build as tsx_build
+    torch.cuda.set_device(0)
+    tsx_build.build()
+    pk = tsx.measure_peaks()
+    stream = torch.cuda.Stream()
+    fn = {"list2640": lambda: extra_list(tsx, pk, stream, steps=args.steps, limit=args.cand_limit),
+          "budget_peg": lambda: extra_budget(tsx, pk, stream),
+          "lnms_code1": lambda: extra_lnms(tsx, pk, stream, None),
+          "emd_code1": lambda: extra_emd(tsx, stream)}[args.workload]
+    with Clocks(0) as clk:
+        d = fn()
+    metric, unit, key = EXTRA_WORKLOADS[args.workload]
+    line = {"metric": metric, "value": d[key], "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": unit != "ms", "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic", "config": {"workload": args.workload}, **d, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     line = None
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload in EXTRA_WORKLOADS:
+        run_extra_alone(args)
         return
     if args.workload == "isfer":
         line = run_isfer(args)

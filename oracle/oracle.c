@@ -20,9 +20,15 @@
  *   sum-product decoder                 exact MAP on a cycle-free code
  *   bisection                           linear scan on the tiny code
  *   importance-sampling weights         closed forms (mu = 0, Gaussian moments)
- *   ordered list over iterations        dense-matrix restatement on the decoder's x_k trace
+ *   best pattern x*                     first minimum in the window, on recounted u_k traces
+ *   IS channel quantizer                ties / saturation; LLRs recomputed from the normals
+ *   ordered list over iterations        dense-matrix restatement on the decoder's x_k trace;
+ *                                       two-stage kstart from recounted converged decodes
  *   layered simulation decoder          hand-computed iterations; QC layer = its rows one by one;
- *                                       saturation of each width; codeword inputs
+ *                                       saturation of each width; codeword inputs; frame channel
+ *   cycles, EMD (Prop. 1)               Table II rows 4-10 (Code 1); Hashimoto-matrix traces;
+ *                                       brute-force walk classes; Table V densities
+ *   iteration budgets                   per-candidate rerun with K = K(I)
  * The decoders themselves are not specified by the paper ("our used version
  * of message passing decoder", Sec. III), so the decoder arithmetic has no
  * paper pin beyond the substitutes above.

@@ -86,8 +86,10 @@ bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_p
         // as many codeword groups as fit (up to one per warp), the warps shared among them
         G = max_warps / (fit < max_warps ? fit : max_warps);
         int work = g.m < g.n ? g.m : g.n;
-        // QC passes run block by block (the variable-node-pass form runs all blocks at once)
-        if (g.kind == TSX_CODE_QC && kind != kLayPairVn && g.Z < work) work = g.Z;
+        // QC passes run block by block (the variable-node-pass form, and the sampling kernel for
+        // check degree > 8, run all blocks at once)
+        const bool flat = kind == kLayPairVn || (kind == kLayIs && g.dc_max > 8);
+        if (g.kind == TSX_CODE_QC && !flat && g.Z < work) work = g.Z;
         int gmax = work / 32;
         if (gmax < 1) gmax = 1;
         if (G > gmax) G = gmax;

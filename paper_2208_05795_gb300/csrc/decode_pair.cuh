@@ -86,7 +86,9 @@ struct Half {
 // after each check pass from the stored messages, instead of the
 // accumulating second buffer -- 4 bytes per node less, for codes whose
 // two-buffer layout does not fit a CTA.
-template <bool QC, int DC, bool EXACT, bool I8, bool VN = false>
+// FLAT (QC, accumulating form): the check pass runs over all row blocks at
+// once, as the VN form does, so that a group may be wider than Z rows.
+template <bool QC, int DC, bool EXACT, bool I8, bool VN = false, bool FLAT = false>
 struct PairDecoder {
     static constexpr int RSZ = I8 ? 2 : 4;  // bytes of one packed message pair
     const DevCode &g;
@@ -132,6 +134,13 @@ struct PairDecoder {
         q = vminu2(vmaxu2(x - y + pc.B2, pc.LO2), pc.HI2);
         a = vmaxu2(q, (~q) + 0x00010001u);
     }
+    // the same without clamping the value: d = (P - r) + beta, which the
+    // launcher's bounds keep inside each half and which has the sign of
+    // clamp(P - r), and a = min(|P - r|, sat) + beta, the clamped magnitude
+    __device__ __forceinline__ void edge_da(unsigned x, unsigned y, unsigned &d, unsigned &a) const {
+        d = x - y + pc.B2;
+        a = vminu2(vmaxu2(d, (~d) + 0x00010001u), pc.BS2);
+    }
 
     // the new message of an edge from its q'', |q|, the check's min1, the
     // two output magnitudes and the sign parity of all its edges
@@ -166,7 +175,7 @@ struct PairDecoder {
                 const unsigned y = ldy<MASK>(re(p), km, kb);
                 sp ^= x;
                 unsigned q, a;
-                edge_q(x, y, q, a);
+                edge_da(x, y, q, a);
                 sx ^= q;
                 m2 = vminu2(m2, vmaxu2(m1, a));
                 m1 = vminu2(m1, a);
@@ -324,7 +333,7 @@ struct PairDecoder {
         const unsigned char *Pc = (const unsigned char *)Pcur;
         unsigned char *Pn = (unsigned char *)Pnext;
         const int Z = g.Z;
-        if constexpr (QC && VN) {
+        if constexpr (QC && (VN || FLAT)) {
             // all row blocks at once (check c = i Z + r), so that a group may be wider than Z rows
             const unsigned zm = Z > 1 ? 0xFFFFFFFFu / (unsigned)Z + 1u : 0u;  // c / Z = umulhi(c, zm), c < 2^16
             for (int c = gp.gt; c < g.m; c += gp.T) {
@@ -392,7 +401,7 @@ struct PairDecoder {
         } else {
             const int m = g.m;
             for (int c = gp.gt; c < m; c += gp.T) {
-                const int e0 = sg.c_ptr[c];
+                const int e0 = EXACT ? c * DC : (int)sg.c_ptr[c];  // check-regular: rows of DC edges
                 const int deg = EXACT ? DC : sg.c_ptr[c + 1] - e0;
                 const int f = check_node<MASK>(
                     deg, km, kb, writeR, Pc, Pn, [&](int p) { return 4 * (int)sg.c_vn[e0 + p]; },

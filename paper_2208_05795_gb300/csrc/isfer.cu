@@ -39,6 +39,8 @@ struct IsArgs {
 // ---------------------------------------------------------------------------
 // the sampling kernel: two samples per lane, as the enumeration decoder
 // ---------------------------------------------------------------------------
+// QC codes of check degree > 8 run the check pass over all row blocks at once
+// (FLAT), so that one sample pair can take more warps than Z / 32.
 template <bool QC, int DC, bool EXACT>
 __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsArgs ia, SlotLayout lay, int G) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -74,7 +76,7 @@ __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsA
     pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
-    PairDecoder<QC, DC, EXACT, false> dec{g, sg, gp, pc, Rb};
+    PairDecoder<QC, DC, EXACT, false, false, QC && (DC > 8)> dec{g, sg, gp, pc, Rb};
 
     for (int w = gp.gt; w < nw; w += gp.T) Tm[w] = 0u;
     gp.sync();

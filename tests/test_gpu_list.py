@@ -54,7 +54,7 @@ def test_qc96_list_mode_bit_exact(kstart):
     assert len(v["keys"]) > 300 and s["list_patterns"] > 0
 
 
-@pytest.mark.parametrize("name,n", [("peg1008", 2500), ("qc2640", 400)])
+@pytest.mark.parametrize("name,n", [("peg1008", 1200), ("qc2640", 150)])
 def test_list_mode_shard_bit_exact(name, n):
     # a range of the full-size workloads' candidates, two-stage window start
     w = synth.workload(name)
