@@ -105,7 +105,7 @@ def alu_roofline(eu_per_launch, ms_launch, pk, sm_mhz, packed=True, traffic=None
 # name -> (metric, unit, key of the value in the extra's summary)
 EXTRA_WORKLOADS = {
     "list2640": ("ordered-list distinct trapping sets/s", "trapping sets/s", "distinct_ts_per_s"),
-    "budget_peg": ("iteration-budget speed-up over K for all", "x", "speedup"),
+    "budget_code1": ("iteration-budget speed-up over K for all", "x", "speedup"),
     "lnms_code1": ("layered-decoder frames/s", "frames/s", "frames_per_s"),
     "emd_code1": ("EMD spectrum search time", "ms", "ms"),
 }
@@ -902,20 +902,24 @@ def extra_list(tsx, pk, stream, steps=2, limit=-1):
 
 
 def extra_budget(tsx, pk, stream):
-    """Cycle-density iteration budgets (Sec. III, Table V) on the PEG code's
-    first 2 million candidates: K(I) = 10 + ceil(40 * 4 / (4 + W(I)))."""
-    w = synth.workload("peg1008")
-    c = tsx.load_code(w["code"], stream=stream)
-    p = dict(params_of(w, "nms16"), cand_end=2_000_000)
+    """Cycle-density iteration budgets (Sec. III, Table V) on Code 1 of Table V
+    (girth 4; the PEG code has girth 8, so no 4- or 6-cycles and no budget):
+    every candidate of size 1-2, K = 50, s = 12, against
+    K(I) = 10 + ceil(40 * 4 / (4 + W(I)))."""
+    E, Z = _code1()
+    c = tsx.load_code(synth.qc_code(E, Z), stream=stream)
+    p = dict(decoder="nms16", K=50, base_llr=16, amp_steps=12, max_size=2, cycle_len=0)
     out = {}
     for name, extra in (("plain", {}), ("budget", dict(budget_wref=4, budget_kmin=10))):
         tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, **p, **extra))
         ms, st = _timed(lambda: tsx.ts_list_view(tsx.enumerate_ts(c, stream=stream, **p, **extra)), stream)
         out[name] = {"ms": ms, "edge_updates": st["stats"]["edge_updates"], "n_ts": st["stats"]["n_ts"],
-                     "keys": set(st["keys"])}
+                     "n_cand": st["stats"]["n_cand"], "keys": set(st["keys"])}
     kp, kb = out["plain"].pop("keys"), out["budget"].pop("keys")
-    return {"workload": "peg1008[:2000000] with and without iteration budgets (wref 4, kmin 10)", **out,
+    return {"workload": "Code 1 (Table V), candidates of size 1-2, K 50, s 12, with and without iteration budgets "
+                        "(wref 4, kmin 10)", **out,
             "speedup": out["plain"]["ms"] / out["budget"]["ms"],
+            "edge_update_ratio": out["budget"]["edge_updates"] / max(1, out["plain"]["edge_updates"]),
             "sets_kept": len(kp & kb) / max(1, len(kp)), "sets_new": len(kb - kp)}
 
 
@@ -1018,7 +1022,7 @@ def run_extra_alone(args):
     pk = tsx.measure_peaks()
     stream = torch.cuda.Stream()
     fn = {"list2640": lambda: extra_list(tsx, pk, stream, steps=args.steps, limit=args.cand_limit),
-          "budget_peg": lambda: extra_budget(tsx, pk, stream),
+          "budget_code1": lambda: extra_budget(tsx, pk, stream),
           "lnms_code1": lambda: extra_lnms(tsx, pk, stream, None),
           "emd_code1": lambda: extra_emd(tsx, stream)}[args.workload]
     with Clocks(0) as clk:

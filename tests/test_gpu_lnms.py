@@ -33,8 +33,10 @@ def test_lnms_decode_bit_exact(name, widths):
     rng = np.random.default_rng(zlib.crc32(repr((name, widths)).encode()))
     nf = 300
     lim = (1 << (lb - 1)) - 1
-    # noisy frames around +3 with some strongly negative values (beyond the width, saturated on both sides)
-    llr = np.clip(np.round(rng.normal(3.0, 3.0, (nf, g.n))), -100, 100).astype(np.int8)
+    # frames around +3 at three noise levels (most decode at the lowest, few at the highest), with values
+    # beyond the LLR width on both sides (saturated)
+    sd = np.array([1.0, 2.0, 3.0])[np.arange(nf) % 3][:, None]
+    llr = np.clip(np.round(rng.normal(3.0, 1.0, (nf, g.n)) * sd + 3.0 * (1 - sd)), -100, 100).astype(np.int8)
     d = torch.from_numpy(llr).cuda()
     fail = torch.zeros(nf, dtype=torch.uint8, device="cuda")
     it = torch.zeros(nf, dtype=torch.int32, device="cuda")

@@ -31,9 +31,11 @@ GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def _golden(name):
-    z = np.load(os.path.join(GOLDEN, f"spectrum_{name}.npz"))
+    with np.load(os.path.join(GOLDEN, f"spectrum_{name}.npz")) as f:
+        z = {k: f[k] for k in f.files}  # each access of the archive decompresses again: read once
     meta = json.loads(str(z["meta"]))
-    keys = [tuple(int(x) for x in z["keys"][z["key_off"][i]:z["key_off"][i + 1]]) for i in range(len(z["ts_a"]))]
+    flat, off = z["keys"].tolist(), z["key_off"].tolist()
+    keys = [tuple(flat[off[i]:off[i + 1]]) for i in range(len(z["ts_a"]))]
     return z, meta, keys
 
 
