@@ -67,7 +67,7 @@ ALG_OPS_PER_EDGE = 12
 ALG_SMEM_BYTES_PER_EDGE = 4
 # DRAM bytes (read + write) an ncu capture measured for the PEG decode launch over its first
 # 40,000 candidates; None until captured for the kernel as it stands
-PAIR_KERNEL_DRAM_BYTES_40K = None
+PAIR_KERNEL_DRAM_BYTES_40K = 726272.0
 SM_MAX_MHZ = 2070.0
 try:  # the maximum SM clock measured on this machine, when the measurement file is present
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as _f:
@@ -108,6 +108,7 @@ EXTRA_WORKLOADS = {
     "budget_code1": ("iteration-budget speed-up over K for all", "x", "speedup"),
     "lnms_code1": ("layered-decoder frames/s", "frames/s", "frames_per_s"),
     "emd_code1": ("EMD spectrum search time", "ms", "ms"),
+    "spa_peg": ("sum-product edge-updates/s", "edge-updates/s", "edge_updates_per_s"),
 }
 
 
@@ -923,6 +924,35 @@ def extra_budget(tsx, pk, stream):
             "sets_kept": len(kp & kb) / max(1, len(kp)), "sets_new": len(kb - kp)}
 
 
+# single-precision operations of one sum-product edge update, counted from
+# the decoder's series (IEEE-rounded adds, multiplies and divides, no fused
+# multiply-add): tanh of q/2 (range reduction, the degree-9 expm1 Horner
+# sum, e / (e + 2): about 42), the product over the other d - 1 = 5 edges
+# (5), atanh of the product (series or frexp/log series, about 30), the
+# clips, x2 and the variable-node add and extrinsic subtract (about 7)
+SPA_OPS_PER_EDGE = 84
+
+
+def extra_spa(tsx, pk, stream, sm_mhz):
+    """The single-precision sum-product decoder on the PEG code's first
+    200,000 candidates (K = 50, 12 halvings of the amplitude)."""
+    w = synth.workload("peg1008")
+    c = tsx.load_code(w["code"], stream=stream)
+    p = dict(params_of(w, "spa"), cand_end=200_000)
+    tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, **p))
+    ms, st = _timed(lambda: tsx.ts_list_stats(tsx.enumerate_ts(c, stream=stream, **p)), stream)
+    mhz = sm_mhz or SM_MAX_MHZ
+    peak = pk["fp32_fma_per_clk_sm"] * pk["num_sms"] * mhz * 1e6 / SPA_OPS_PER_EDGE
+    achieved = st["edge_updates"] / (st["ms_decode"] / 1e3)
+    return {"workload": "peg1008[:200000], single-precision sum-product, K 50, s 12", "ms_per_step": ms,
+            "edge_updates_per_s": st["edge_updates"] / (ms / 1e3), "n_ts": st["n_ts"], "decodes": st["decodes"],
+            "roofline": {"bound": "fp32", "achieved": achieved, "peak": peak, "unit": "edge-updates/s",
+                         "frac": achieved / peak,
+                         "note": f"{SPA_OPS_PER_EDGE} single-precision operations per edge update against the "
+                                 "measured FP32 lane rate; decode kernel time"},
+            "gpu_launches": 10}
+
+
 def extra_lnms(tsx, pk, stream, sm_mhz):
     """The paper's simulation decoder (layered min-sum, 4/4/6 bits, 20
     iterations) on Code 1 of Table V ((2560, 2048), 4 x 20 base, Z = 128),
@@ -1001,6 +1031,7 @@ def run_extras(args, tsx, pk):
     for name, fn in (("list_mode", lambda: extra_list(tsx, pk, stream)),
                      ("iteration_budget", lambda: extra_budget(tsx, pk, stream)),
                      ("layered_simulation", lambda: extra_lnms(tsx, pk, stream, sm)),
+                     ("sum_product", lambda: extra_spa(tsx, pk, stream, sm)),
                      ("emd_spectrum", lambda: extra_emd(tsx, stream))):
         t0 = time.perf_counter()
         try:
@@ -1024,7 +1055,8 @@ def run_extra_alone(args):
     fn = {"list2640": lambda: extra_list(tsx, pk, stream, steps=args.steps, limit=args.cand_limit),
           "budget_code1": lambda: extra_budget(tsx, pk, stream),
           "lnms_code1": lambda: extra_lnms(tsx, pk, stream, None),
-          "emd_code1": lambda: extra_emd(tsx, stream)}[args.workload]
+          "emd_code1": lambda: extra_emd(tsx, stream),
+          "spa_peg": lambda: extra_spa(tsx, pk, stream, None)}[args.workload]
     with Clocks(0) as clk:
         d = fn()
     metric, unit, key = EXTRA_WORKLOADS[args.workload]

@@ -568,6 +568,7 @@ typedef struct {
     double smem_bytes_per_clk_sm;  /* shared-memory load bytes (16-byte vector loads, no bank conflict) */
     double sfu_ops_per_clk_sm;     /* special-function lane operations (ex2.approx.f32) */
     double fp32_fma_per_clk_sm;    /* single-precision fused multiply-add lane operations */
+    double imad_ops_per_clk_sm;    /* 32-bit integer multiply-add lane operations (mad.lo.u32) */
 } tsx_peaks;
 TSX_API int measure_peaks(tsx_peaks *out, void *stream);
 

@@ -104,7 +104,7 @@ class ServerStats(C.Structure):
 class Peaks(C.Structure):
     _fields_ = [("num_sms", C.c_int32), ("int32_ops_per_clk_sm", C.c_double), ("u16x2_ops_per_clk_sm", C.c_double),
                 ("smem_bytes_per_clk_sm", C.c_double), ("sfu_ops_per_clk_sm", C.c_double),
-                ("fp32_fma_per_clk_sm", C.c_double)]
+                ("fp32_fma_per_clk_sm", C.c_double), ("imad_ops_per_clk_sm", C.c_double)]
 
 
 class LnmsParams(C.Structure):

@@ -515,7 +515,7 @@ int code_device(const tsx_code *c) { return c->device; }
 int enum_params_to_decode(const tsx_enum_params *p, DecodeParams *dp) {
     const int st = check_params(*p);
     if (st != TSX_OK) return st;
-    dp->decoder = p->decoder; dp->K = p->K; dp->base_llr = p->base_llr; dp->sat = p->sat;
+    dp->decoder = p->decoder; dp->K = p->K; dp->unit = 1; dp->base_llr = p->base_llr; dp->sat = p->sat;
     dp->alpha_num = p->alpha_num; dp->alpha_shift = p->alpha_shift; dp->amp_steps = p->amp_steps;
     dp->spa_clip = p->spa_clip; dp->spa_amax = p->spa_amax;
     return TSX_OK;
@@ -626,7 +626,7 @@ static int prepare_list(tsx_code *code, const tsx_enum_params *params, cudaStrea
     }
     if (L->pool_cap > 0xfffffff0LL) L->pool_cap = 0xfffffff0LL;
     DecodeParams &dp = L->dp;
-    dp.decoder = p.decoder; dp.K = p.K; dp.base_llr = p.base_llr; dp.sat = p.sat;
+    dp.decoder = p.decoder; dp.K = p.K; dp.unit = 1; dp.base_llr = p.base_llr; dp.sat = p.sat;
     dp.alpha_num = p.alpha_num; dp.alpha_shift = p.alpha_shift; dp.amp_steps = p.amp_steps;
     dp.spa_clip = p.spa_clip; dp.spa_amax = p.spa_amax;
 

@@ -110,6 +110,25 @@ __global__ void __launch_bounds__(kThreads) smem_probe(unsigned *sink, Span *sp)
     if ((acc.x ^ acc.y ^ acc.z ^ acc.w) == 0x12345678u) sink[0] = acc.x;
 }
 
+// 32-bit integer multiply-add (mad.lo.u32 with register operands): the
+// integer work the FMA pipe can take
+__global__ void __launch_bounds__(kThreads) imad_probe(unsigned k1, unsigned k2, unsigned *sink, Span *sp) {
+    unsigned a[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) a[u] = threadIdx.x * 2654435761u + u;
+    long long t0;
+    span_begin(t0);
+    for (int it = 0; it < kIters; it++) {
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a[u]) : "r"(k1), "r"(k2));
+    }
+    span_end(t0, sp);
+    unsigned x = 0;
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) x ^= a[u];
+    if (x == 0x12345678u) sink[0] = x;
+}
+
 // the special-function unit: ex2.approx.f32
 __global__ void __launch_bounds__(kThreads) sfu_probe(float *sink, Span *sp) {
     float a[kUnroll];
@@ -213,6 +232,8 @@ extern "C" int measure_peaks(tsx_peaks *out, void *stream) {
         out->sfu_ops_per_clk_sm = rate(h, thr_ops / 4, num_sms);
     if (st == TSX_OK && (st = run_probe(fma_probe, num_sms, s, d_sp, h, 0.999f, 1e-4f, (float *)sink)) == TSX_OK)
         out->fp32_fma_per_clk_sm = rate(h, thr_ops, num_sms);
+    if (st == TSX_OK && (st = run_probe(imad_probe, num_sms, s, d_sp, h, 0x9E3779B9u, 0x7F4A7C15u, sink)) == TSX_OK)
+        out->imad_ops_per_clk_sm = rate(h, thr_ops, num_sms);
     cudaStreamSynchronize(s);
     cudaFree(d_sp);
     cudaFree(sink);
