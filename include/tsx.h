@@ -257,8 +257,10 @@ TSX_API void free_ts_list(tsx_ts_list *list);
 
 /* ---- tile autotuner (no counterpart in the paper) ---------------------
  * Picks the decode tile for `code` under `params`: the number of warps that
- * share one pair of codewords (1, 2, 4 or 8, at most one warp per 32 rows of
- * the smallest pass) and, for the int16 min-sum decoder with sat <= 169, int8
+ * share one pair of codewords (the automatic shape -- as many pairs as fit a
+ * CTA, the warps shared among them, reported as 0 -- or 1, 2, 4 or 8, at most
+ * one warp per 32 rows of the smallest pass) and, for the int16 min-sum
+ * decoder with sat <= 169, int8
  * message storage (which gives the same results).  Each choice decodes the
  * first num_sms * 256 canonical candidates once after one warm-up run, timed
  * with CUDA events on `stream` (synchronizes); the fastest is written to

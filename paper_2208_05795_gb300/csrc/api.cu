@@ -515,7 +515,7 @@ int code_device(const tsx_code *c) { return c->device; }
 int enum_params_to_decode(const tsx_enum_params *p, DecodeParams *dp) {
     const int st = check_params(*p);
     if (st != TSX_OK) return st;
-    dp->decoder = p->decoder; dp->K = p->K; dp->unit = 1; dp->base_llr = p->base_llr; dp->sat = p->sat;
+    dp->decoder = p->decoder; dp->K = p->K; dp->base_llr = p->base_llr; dp->sat = p->sat;
     dp->alpha_num = p->alpha_num; dp->alpha_shift = p->alpha_shift; dp->amp_steps = p->amp_steps;
     dp->spa_clip = p->spa_clip; dp->spa_amax = p->spa_amax;
     return TSX_OK;
@@ -626,7 +626,7 @@ static int prepare_list(tsx_code *code, const tsx_enum_params *params, cudaStrea
     }
     if (L->pool_cap > 0xfffffff0LL) L->pool_cap = 0xfffffff0LL;
     DecodeParams &dp = L->dp;
-    dp.decoder = p.decoder; dp.K = p.K; dp.unit = 1; dp.base_llr = p.base_llr; dp.sat = p.sat;
+    dp.decoder = p.decoder; dp.K = p.K; dp.base_llr = p.base_llr; dp.sat = p.sat;
     dp.alpha_num = p.alpha_num; dp.alpha_shift = p.alpha_shift; dp.amp_steps = p.amp_steps;
     dp.spa_clip = p.spa_clip; dp.spa_amax = p.spa_amax;
 
@@ -814,7 +814,8 @@ extern "C" int tune_tile(tsx_code *code, const tsx_enum_params *params, void *st
     if (params->decoder == TSX_DEC_NMS_I16 && params->sat <= 169) decs.push_back(TSX_DEC_NMS_I8);
     int work = std::min(g.m, g.n);
     if (g.kind == TSX_CODE_QC) work = std::min(work, g.Z);
-    std::vector<int> Gs{1};
+    // 0: the automatic shape (as many codeword groups as fit, the warps shared among them)
+    std::vector<int> Gs{0, 1};
     for (int G = 2; G <= 8 && G * 32 <= std::max(32, work); G *= 2) Gs.push_back(G);
     tsx_enum_params t = *params;
     t.record_candidates = 0;

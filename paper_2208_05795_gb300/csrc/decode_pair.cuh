@@ -60,35 +60,12 @@ __device__ __forceinline__ void red_add(unsigned char *addr, unsigned v) {
                  : "memory");
 }
 
-// Shared-memory accesses by 32-bit shared-window address, and a
-// multiply-add whose multiplier the compiler cannot see: the add and shift
-// work of the address and offset arithmetic then issues as IMAD on the FMA
-// pipe instead of on the integer ALU, which the check pass saturates.
-__device__ __forceinline__ unsigned imad(unsigned a, unsigned b, unsigned c) {
-    unsigned d;
-    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
-    return d;
-}
-__device__ __forceinline__ unsigned lds32(unsigned addr) {
-    unsigned v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-    return v;
-}
-__device__ __forceinline__ void sts32(unsigned addr, unsigned v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ void red32(unsigned addr, unsigned v) {
-    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-
 constexpr unsigned kBeta = 0x8000u;
 
 struct PairConst {
     unsigned B2, BS2, LO2, HI2, BETA2, amask2;  // LO2 / HI2: clamp bounds of q'' = q + beta
     unsigned BAN2;  // BETA2 * alpha_num: (m - beta) an = m an - BAN2 (mod 2^32)
     int B, sat, an, as;
-    unsigned one, four, mone;  // 1, 4, 0xFFFFFFFF from a kernel parameter (multipliers of imad)
 };
 
 // per-half schedule state (uniform across the group)
@@ -223,58 +200,6 @@ struct PairDecoder {
                     const unsigned rn = edge_out(qs[p], as_[p], m1, oo, sxk);
                     stR(re(p), rn);
                     if constexpr (!VN) red_add(Pn + po[p], rn);
-                }
-            }
-        }
-        return (int)((unsat >> 15) & 0x00010001u);
-    }
-
-    // check_node_regs for 16-bit storage in the accumulating form, by shared
-    // addresses: vn(p) = index of the p-th variable node, ra(p) = shared
-    // address of the p-th message; the same arithmetic with the add-like
-    // steps on IMAD (see imad()).
-    template <bool MASK, class VI, class RA>
-    __device__ __forceinline__ int check_node_sa(int deg, unsigned km, unsigned kb, bool writeR, unsigned Pcs,
-                                                 unsigned Pns, VI vn, RA ra) const {
-        unsigned sp = 0, sx = 0, m1 = pc.BS2, m2 = pc.BS2;
-        unsigned qs[DC], as_[DC], vi[DC];
-#pragma unroll
-        for (int p = 0; p < DC; p++) {
-            if (EXACT || p < deg) {
-                vi[p] = (unsigned)vn(p);
-                const unsigned x = lds32(imad(vi[p], pc.four, Pcs));
-                unsigned y = lds32(ra(p));
-                if constexpr (MASK) y = (y & km) | kb;
-                sp ^= x;
-                const unsigned d = x - y + pc.B2;                      // (P - r) + beta per half
-                const unsigned nd = imad(d, pc.mone, 0x00010000u);     // 2 beta - d per half
-                const unsigned a = vminu2(vmaxu2(d, nd), pc.BS2);      // min(|P - r|, sat) + beta
-                sx ^= d;
-                m2 = vminu2(m2, vmaxu2(m1, a));
-                m1 = vminu2(m1, a);
-                qs[p] = d;
-                as_[p] = a;
-            }
-        }
-        const unsigned dodd = (deg & 1) ? 0x80008000u : 0u;
-        const unsigned unsat = (sp ^ dodd) & 0x80008000u;
-        if (writeR) {
-            const unsigned o1 = ((m1 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
-            const unsigned o2 = ((m2 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
-            const unsigned p1 = imad(o1, pc.one, pc.B2), n1 = imad(o1, pc.mone, pc.B2);
-            const unsigned p2 = imad(o2, pc.one, pc.B2), n2 = imad(o2, pc.mone, pc.B2);
-            const unsigned m1n = 0x7FFF7FFFu - m1;
-            const unsigned sxk = sx ^ (((deg - 1) & 1) ? 0x80008000u : 0u);
-#pragma unroll
-            for (int p = 0; p < DC; p++) {
-                if (EXACT || p < deg) {
-                    const unsigned neg = spread15(sxk ^ qs[p]);               // others' sign product < 0
-                    const unsigned ne = spread15(imad(as_[p], pc.one, m1n));  // |q_p| != min1
-                    const unsigned t1 = (n1 & neg) | (p1 & ~neg);
-                    const unsigned t2 = (n2 & neg) | (p2 & ~neg);
-                    const unsigned rn = (t1 & ne) | (t2 & ~ne);
-                    sts32(ra(p), rn);
-                    red32(imad(vi[p], pc.four, Pns), rn);
                 }
             }
         }
@@ -473,20 +398,6 @@ struct PairDecoder {
                     }
                 }
             }
-        } else if constexpr (DC <= 8 && !I8 && !VN) {
-            // by shared addresses: message (c, p) at Rs + 4 (p m + c)
-            const int m = g.m;
-            const unsigned Pcs = smem_addr(Pc), Pns = smem_addr(Pn), Rs = smem_addr(Rb);
-            const unsigned m4 = imad((unsigned)m, pc.four, 0u);
-            for (int c = gp.gt; c < m; c += gp.T) {
-                const int e0 = EXACT ? c * DC : (int)sg.c_ptr[c];  // check-regular: rows of DC edges
-                const int deg = EXACT ? DC : sg.c_ptr[c + 1] - e0;
-                const unsigned rc = imad((unsigned)c, pc.four, Rs);
-                const int f = check_node_sa<MASK>(
-                    deg, km, kb, writeR, Pcs, Pns, [&](int p) { return (int)sg.c_vn[e0 + p]; },
-                    [&](int p) { return imad((unsigned)p, m4, rc); });
-                u += f;
-            }
         } else {
             const int m = g.m;
             for (int c = gp.gt; c < m; c += gp.T) {
@@ -624,9 +535,6 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
-    pc.one = (unsigned)dp.unit;
-    pc.four = 4u * pc.one;
-    pc.mone = 0u - pc.one;
     PairDecoder<QC, DC, EXACT, I8, VN> dec{g, sg, gp, pc, Rb};
 
     const long long total = (long long)b.ctr->n_cand_total;

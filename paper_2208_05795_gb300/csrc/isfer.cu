@@ -76,9 +76,6 @@ __global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsA
     pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
-    pc.one = (unsigned)dp.unit;
-    pc.four = 4u * pc.one;
-    pc.mone = 0u - pc.one;
     PairDecoder<QC, DC, EXACT, false, false, QC && (DC > 8)> dec{g, sg, gp, pc, Rb};
 
     for (int w = gp.gt; w < nw; w += gp.T) Tm[w] = 0u;
@@ -279,7 +276,6 @@ static int is_plan(tsx_code *code, const int32_t *ts_vars, int32_t a, const tsx_
     J.g = g;
     J.dp.decoder = TSX_DEC_NMS_I16;
     J.dp.K = p->K;
-    J.dp.unit = 1;
     J.dp.sat = p->sat;
     J.dp.alpha_num = p->alpha_num;
     J.dp.alpha_shift = p->alpha_shift;

@@ -90,7 +90,6 @@ constexpr int kPoolHdr = 4;
 struct DecodeParams {
     int decoder;  // TSX_DEC_*
     int K;
-    int unit;     // 1 (a multiplier the kernels take from their parameters)
     int base_llr;
     int sat;
     int alpha_num, alpha_shift;

@@ -124,3 +124,26 @@ def test_server_rejects_bad_jobs(mix):
             srv.submit_is_fer(handles[0], [10 ** 6], n_samples=10)
         jid = srv.submit_is_fer(handles[0], [0, 1, 2], n_samples=1000)
         assert srv.wait(jid)["status"] == 0
+
+
+def test_server_timed_stream_with_list_and_budget_jobs(mix):
+    # jobs arrive one by one (seeded exponential gaps) while others run, and the
+    # mix includes an ordered-list job and a job with iteration budgets; each
+    # result must still equal the stand-alone call's
+    import time
+    handles, jobs, alone = mix
+    extra = [("enum", handles[0], tsx.make_params(**dict(ENUM, max_size=3, list_mode=1, kstart=-1))),
+             ("enum", handles[1], tsx.make_params(**dict(ENUM, budget_wref=4, budget_kmin=5, cand_end=6000)))]
+    extra_alone = [tsx.ts_list_view(tsx.enumerate_ts(h, p)) for _, h, p in extra]
+    all_jobs, all_alone = jobs + extra, alone + extra_alone
+    order = np.random.default_rng(17).permutation(len(all_jobs))
+    gaps = np.random.default_rng(18).exponential(0.004, len(all_jobs))
+    with tsx.Server(max_jobs=4, chunk_candidates=2048, chunk_samples=8192) as srv:
+        ids = {}
+        for k, g in zip(order, gaps):
+            time.sleep(float(g))
+            ids[k] = _submit_all(srv, [all_jobs[k]])[0]
+        sel = sorted(ids)
+        _check_same(srv, [all_jobs[k] for k in sel], [ids[k] for k in sel], [all_alone[k] for k in sel])
+        st = srv.stats()
+        assert st["done"] == len(all_jobs) and st["failed"] == 0
