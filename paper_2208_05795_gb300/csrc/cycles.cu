@@ -82,25 +82,27 @@ __device__ int walk_reps(const int *vs, const int *cs, int L) {
 }
 
 // walks[rep * (kLmax + 1) + l]: closed walks of l variable nodes from the
-// representative; hist2[l * kEmdBins + e]: sum of 2l / (p r) over them by EMD
-__global__ void __launch_bounds__(256) cycle_kernel(DevCode g, int lmax, long long n_prefix,
+// representative; hist2[l * kEmdBins + e]: sum of 2l / (p r) over them by EMD.
+// Thread id = (rep, t_1, p_1, ..., t_pd, p_pd): the walk's first pd steps
+// (check t of the last node, then node p of that check); the walks that
+// close within the prefix are counted by the thread whose deeper indices are
+// all 0, and the rest of the search runs from the prefix's last node.
+__global__ void __launch_bounds__(256) cycle_kernel(DevCode g, int lmax, int pd, long long n_prefix,
                                                     unsigned long long *walks, unsigned long long *hist2) {
     const int dvm = g.dv_max, dcm = g.dc_max;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n_prefix;
          id += (long long)gridDim.x * blockDim.x) {
         long long x = id;
-        const int p2 = (int)(x % dcm); x /= dcm;
-        const int t2 = (int)(x % dvm); x /= dvm;
-        const int p1 = (int)(x % dcm); x /= dcm;
-        const int t1 = (int)(x % dvm); x /= dvm;
+        int tt[4], pp[4];
+        for (int lvl = pd; lvl >= 1; lvl--) {
+            pp[lvl] = (int)(x % dcm);
+            x /= dcm;
+            tt[lvl] = (int)(x % dvm);
+            x /= dvm;
+        }
         const int rep = (int)x;
         int vs[kLmax], cs[kLmax + 1];
         vs[0] = rep_vn(g, rep);
-        if (t1 >= vn_degree(g, vs[0])) continue;
-        cs[1] = vn_check(g, vs[0], t1);
-        if (p1 >= cn_degree(g, cs[1])) continue;
-        vs[1] = cn_vn(g, cs[1], p1);
-        if (vs[1] == vs[0]) continue;
         unsigned long long cnt[kLmax + 1] = {0, 0, 0, 0, 0, 0, 0};
         // the walks that close at v_d through a check of v_d holding v0
         auto closure = [&](int d) {
@@ -115,57 +117,71 @@ __global__ void __launch_bounds__(256) cycle_kernel(DevCode g, int lmax, long lo
                 if (hist2) atomicAdd(&hist2[L * kEmdBins + emd_of(g, vs, L)], (unsigned long long)(2 * L / walk_reps(vs, cs, L)));
             }
         };
-        // length 4 closes at v1: once per (v0, c1, v1), by the first (t2, p2)
-        if (t2 == 0 && p2 == 0 && lmax >= 2) closure(1);
-        if (lmax >= 3 && t2 < vn_degree(g, vs[1])) {
-            cs[2] = vn_check(g, vs[1], t2);
-            if (cs[2] != cs[1] && p2 < cn_degree(g, cs[2])) {
-                vs[2] = cn_vn(g, cs[2], p2);
-                if (vs[2] != vs[1]) {
-                    int ti[kLmax], pi[kLmax];
-                    int d = 2;
-                    bool enter = true;
-                    while (d >= 2) {
-                        if (enter) {
-                            closure(d);
-                            if (d >= lmax - 1) {
-                                d--;
-                                enter = false;
-                                continue;
+        int d = 0;
+        bool ok = true;
+        for (int lvl = 1; lvl <= pd && ok; lvl++) {
+            const int v = vs[lvl - 1];
+            if (tt[lvl] >= vn_degree(g, v)) { ok = false; break; }
+            const int c = vn_check(g, v, tt[lvl]);
+            if (lvl > 1 && c == cs[lvl - 1]) { ok = false; break; }
+            if (pp[lvl] >= cn_degree(g, c)) { ok = false; break; }
+            const int u = cn_vn(g, c, pp[lvl]);
+            if (u == v) { ok = false; break; }
+            cs[lvl] = c;
+            vs[lvl] = u;
+            d = lvl;
+            bool zero_below = true;
+            for (int l2 = lvl + 1; l2 <= pd; l2++) zero_below = zero_below && tt[l2] == 0 && pp[l2] == 0;
+            if (zero_below) closure(lvl);
+            if (lvl >= lmax - 1) {  // no longer walk needed; deeper prefix indices count nothing
+                ok = zero_below;
+                break;
+            }
+        }
+        if (ok && d == pd && d < lmax - 1) {
+            int ti[kLmax], pi[kLmax];
+            ti[d] = 0;
+            pi[d] = 0;
+            bool enter = false;  // the prefix's last node is counted already
+            while (d >= pd) {
+                if (enter) {
+                    closure(d);
+                    if (d >= lmax - 1) {
+                        d--;
+                        enter = false;
+                        continue;
+                    }
+                    ti[d] = 0;
+                    pi[d] = 0;
+                }
+                bool pushed = false;
+                const int dv = vn_degree(g, vs[d]);
+                while (ti[d] < dv && !pushed) {
+                    const int c = vn_check(g, vs[d], ti[d]);
+                    if (c != cs[d]) {
+                        const int dc = cn_degree(g, c);
+                        while (pi[d] < dc) {
+                            const int u = cn_vn(g, c, pi[d]);
+                            pi[d]++;
+                            if (u != vs[d]) {
+                                cs[d + 1] = c;
+                                vs[d + 1] = u;
+                                pushed = true;
+                                break;
                             }
-                            ti[d] = 0;
-                            pi[d] = 0;
-                        }
-                        bool pushed = false;
-                        const int dv = vn_degree(g, vs[d]);
-                        while (ti[d] < dv && !pushed) {
-                            const int c = vn_check(g, vs[d], ti[d]);
-                            if (c != cs[d]) {
-                                const int dc = cn_degree(g, c);
-                                while (pi[d] < dc) {
-                                    const int u = cn_vn(g, c, pi[d]);
-                                    pi[d]++;
-                                    if (u != vs[d]) {
-                                        cs[d + 1] = c;
-                                        vs[d + 1] = u;
-                                        pushed = true;
-                                        break;
-                                    }
-                                }
-                            }
-                            if (!pushed) {
-                                ti[d]++;
-                                pi[d] = 0;
-                            }
-                        }
-                        if (pushed) {
-                            d++;
-                            enter = true;
-                        } else {
-                            d--;
-                            enter = false;
                         }
                     }
+                    if (!pushed) {
+                        ti[d]++;
+                        pi[d] = 0;
+                    }
+                }
+                if (pushed) {
+                    d++;
+                    enter = true;
+                } else {
+                    d--;
+                    enter = false;
                 }
             }
         }
@@ -187,10 +203,13 @@ cudaError_t launch_cycles(const DevCode &g, int lmax, unsigned long long *walks,
     if (hist && (e = cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * (kLmax + 1) * kEmdBins, st)) !=
                     cudaSuccess)
         return e;
-    const long long n_prefix = (long long)g.n_rep * g.dv_max * g.dc_max * g.dv_max * g.dc_max;
+    // three-step prefixes for the deep searches (more, shorter subtrees), two otherwise
+    const int pd = lmax >= 5 ? 3 : 2;
+    long long n_prefix = g.n_rep;
+    for (int l = 0; l < pd; l++) n_prefix *= (long long)g.dv_max * g.dc_max;
     long long blocks = (n_prefix + 255) / 256;
-    if (blocks > 65536) blocks = 65536;
-    cycle_kernel<<<(int)blocks, 256, 0, st>>>(g, lmax, n_prefix, walks, hist);
+    if (blocks > 1 << 20) blocks = 1 << 20;
+    cycle_kernel<<<(int)blocks, 256, 0, st>>>(g, lmax, pd, n_prefix, walks, hist);
     return cudaGetLastError();
 }
 

@@ -95,6 +95,19 @@ bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_p
         if (G > gmax) G = gmax;
         if (G > 16) G = 16;
         if (G < 1) G = 1;
+        if (flat && kind == kLayIs && fit == 1) {
+            // one sample pair per CTA: the width (up to max_warps) with the fewest checks per
+            // thread, the narrowest of those (the pass ends at the group barrier)
+            int best = G, best_rows = (g.m + 32 * G - 1) / (32 * G);
+            for (int w = 8; w <= max_warps && w <= gmax; w++) {
+                const int rows = (g.m + 32 * w - 1) / (32 * w);
+                if (rows < best_rows) {
+                    best = w;
+                    best_rows = rows;
+                }
+            }
+            G = best;
+        }
     }
     int gmax_cta = max_warps / G;  // at most 32 * max_warps threads per CTA
     if (gmax_cta < 1) gmax_cta = 1;
@@ -210,7 +223,9 @@ cudaError_t launch_batch(const BatchArgs &items, int n, int variant, const Launc
 
 bool plan_is_shape(const DevCode &g, const DecodeParams &dp, LaunchShape *sh, int num_sms) {
     if (!pair_ok(g, dp)) return false;
-    return plan(g, TSX_DEC_NMS_I16, kLayIs, 0, 0, 0, num_sms, sh);
+    // the flat form (QC, check degree > 8) is launched with up to kIsWarps warps, the others with 16
+    return plan(g, TSX_DEC_NMS_I16, kLayIs, 0, 0, 0, num_sms, sh,
+                g.kind == TSX_CODE_QC && g.dc_max > 8 ? kIsWarps : 16);
 }
 
 bool decode_fits(const DevCode &g, int decoder) {

@@ -42,7 +42,8 @@ struct IsArgs {
 // QC codes of check degree > 8 run the check pass over all row blocks at once
 // (FLAT), so that one sample pair can take more warps than Z / 32.
 template <bool QC, int DC, bool EXACT>
-__global__ void __launch_bounds__(512) is_kernel(DevCode g, DecodeParams dp, IsArgs ia, SlotLayout lay, int G) {
+__global__ void __launch_bounds__(QC && DC > 8 ? 32 * kIsWarps : 512) is_kernel(DevCode g, DecodeParams dp, IsArgs ia,
+                                                                               SlotLayout lay, int G) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SGraph sg = load_tables(g, smem, true);
     __syncthreads();

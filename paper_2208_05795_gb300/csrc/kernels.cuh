@@ -75,6 +75,8 @@ constexpr int kMaxBatch = 64;
 // 20 warps keep the (3,6)-regular general-code variant at 96 registers
 // without spills and measured faster than 16 or 24
 constexpr int kPairWarps = 20;
+// warps per CTA of the importance-sampling kernel's flat form (its launch bound)
+constexpr int kIsWarps = 18;
 struct BatchArgs {
     BatchItem it[kMaxBatch];
 };

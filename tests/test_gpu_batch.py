@@ -118,7 +118,7 @@ def test_tune_tile_keeps_results(small_batch, sat):
     for h in handles:
         t, ms = tsx.tune_tile(h, base)
         assert ms > 0.0
-        assert t.warps_per_cta in (1, 2, 4, 8)
+        assert t.warps_per_cta in (0, 1, 2, 4, 8)  # 0: the automatic shape
         assert t.decoder in (0, 1) and (sat <= 169 or t.decoder == 0)
         tuned.append(t)
     if sat <= 169:
