@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(512) lnms_kernel(DevCode g, LnmsArgs a, LnmsLa
                 const int16_t *rs = sg.rs + i * g.dc_max;
                 for (int r = gp.gt; r < Z; r += gp.T) {
                     int q[DCMAX], vv[DCMAX];
-                    int m1 = 1 << 20, m2 = 1 << 20, imin = -1, neg = 0;
+                    int m1 = 1 << 20, m2 = 1 << 20, neg = 0;
 #pragma unroll
                     for (int p = 0; p < DCMAX; p++) {
                         if (p < deg) {
@@ -150,19 +150,15 @@ __global__ void __launch_bounds__(512) lnms_kernel(DevCode g, LnmsArgs a, LnmsLa
                             q[p] = qq;
                             neg ^= qq < 0;
                             const int mag = abs(qq);
-                            if (mag < m1) {
-                                m2 = m1;
-                                m1 = mag;
-                                imin = p;
-                            } else if (mag < m2) {
-                                m2 = mag;
-                            }
+                            m2 = min(m2, max(m1, mag));  // the two smallest magnitudes, no branch
+                            m1 = min(m1, mag);
                         }
                     }
 #pragma unroll
                     for (int p = 0; p < DCMAX; p++) {
                         if (p < deg) {
-                            const int mn = p == imin ? m2 : m1;
+                            // the smallest of the others: m2 for an edge at the minimum (with a tie m2 = m1)
+                            const int mn = abs(q[p]) == m1 ? m2 : m1;
                             int mag = deg == 1 ? a.lim_c2v : satw((a.an * mn) >> a.as, a.lim_c2v);
                             const int rr = (neg ^ (q[p] < 0)) ? -mag : mag;
                             R[e0 + p * Z + r] = (int8_t)rr;
