@@ -124,6 +124,12 @@ bool plan(const DevCode &g, int decoder, int kind, int G, int groups, int ctas_p
     return true;
 }
 
+// the launch bound of the two-codeword kernel variant launch_pair picks for g
+int pair_warps(const DevCode &g) {
+    const bool reg6 = g.dc_min == 6 && g.dc_max == 6;
+    return pair_kernel_warps(g.kind == TSX_CODE_QC, reg6 ? 6 : g.dc_max <= 8 ? 8 : 32, reg6);
+}
+
 // the two-codeword kernel keeps every biased quantity inside 16 bits
 bool pair_ok(const DevCode &g, const DecodeParams &dp) {
     if (dp.decoder == TSX_DEC_SPA_F32) return false;
@@ -143,8 +149,8 @@ cudaError_t launch_decode(const DevCode &g, const DecodeParams &dp, const EnumBu
                           int ctas_per_sm, int num_sms, int force_scalar, cudaStream_t st) {
     LaunchShape sh;
     // the two-codeword kernel where its bounds hold and its layout fits a CTA
-    const bool pair = !force_scalar && pair_ok(g, dp) && plan(g, dp.decoder, kLayPair, G, groups, ctas_per_sm,
-                                                             num_sms, &sh, kPairWarps);
+    const bool pair = !force_scalar && pair_ok(g, dp) &&
+                      plan(g, dp.decoder, kLayPair, G, groups, ctas_per_sm, num_sms, &sh, pair_warps(g));
     // QC codes of large check degree whose two-buffer layout does not fit: the variable-node-pass form
     if (!pair && !force_scalar && pair_ok(g, dp) && g.kind == TSX_CODE_QC && dp.decoder == TSX_DEC_NMS_I16 &&
         g.dc_max > 8 && plan(g, dp.decoder, kLayPairVn, G, groups, ctas_per_sm, num_sms, &sh, kPairWarps))

@@ -143,7 +143,7 @@ __device__ SGraph load_tables(const DevCode &g, unsigned char *sm, bool pair = f
 // ---------------------------------------------------------------------------
 struct Grp {
     int G, T, gt, lane, gw, bar;
-    int *red;  // [G] reduction scratch (shared)
+    int *red;  // reduction scratch (shared): [0, 16) for sum(), [16, 32) for sum_pass()
     __device__ __forceinline__ void sync() const {
         if (G == 1) __syncwarp();
         else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(T) : "memory");
@@ -159,6 +159,20 @@ struct Grp {
         int s = 0;
         for (int w = 0; w < G; w++) s += red[w];
         sync();
+        return s;
+    }
+    // the same on the second scratch bank without the closing barrier: the
+    // caller passes a group barrier before its next sum_pass
+    __device__ __forceinline__ int sum_pass(int x) const {
+        x = __reduce_add_sync(0xffffffffu, x);
+        if (G == 1) {
+            __syncwarp();
+            return x;
+        }
+        if (lane == 0) red[16 + gw] = x;
+        sync();
+        int s = 0;
+        for (int w = 0; w < G; w++) s += red[16 + w];
         return s;
     }
 };
@@ -245,7 +259,7 @@ __device__ __forceinline__ float spa_atanhf(float p) {
 
 // misc area of a slot
 struct Misc {
-    int red[16];
+    int red[32];
     long long bcast[2];
     int ints[8];
     unsigned long long okd, okit;  // converged decodes of this group and their iterations

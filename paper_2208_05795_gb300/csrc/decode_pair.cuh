@@ -325,7 +325,8 @@ struct PairDecoder {
         return (int)(((unsatA >> 15) & 0x00010001u) + ((unsatB >> 15) & 0x00010001u));
     }
 
-    // check pass; returns u of half 0 in the low 16 bits and half 1 above
+    // check pass; returns u of half 0 in the low 16 bits and half 1 above (the
+    // caller passes a group barrier before the next check pass)
     template <bool MASK>
     __device__ __forceinline__ int check_pass(unsigned km, unsigned kb, bool writeR, const unsigned *Pcur,
                                               unsigned *Pnext) const {
@@ -366,14 +367,12 @@ struct PairDecoder {
                         }
                     }
                     for (int r = gp.gt; r < Z; r += gp.T) {
-                        const int f = check_node<MASK>(
-                            deg, km, kb, writeR, Pc, Pn,
-                            [&](int p) {
-                                const int t = r + rsh[p];
-                                return rjz4[p] + 4 * (int)min((unsigned)t, (unsigned)(t - Z));
-                            },
-                            [&](int p) { return rb + pz[p] + r * RSZ; });
-                        u += f;
+                        const auto pv = [&](int p) {
+                            const int t = r + rsh[p];
+                            return rjz4[p] + 4 * (int)min((unsigned)t, (unsigned)(t - Z));
+                        };
+                        u += check_node<MASK>(deg, km, kb, writeR, Pc, Pn, pv,
+                                              [&](int p) { return rb + pz[p] + r * RSZ; });
                     }
                 } else {
                     const int32_t *rjz = sg.rjz + i * g.dc_max;
@@ -409,7 +408,7 @@ struct PairDecoder {
                 u += f;
             }
         }
-        return gp.sum(u);
+        return gp.sum_pass(u);
     }
 
     __device__ __forceinline__ int vdeg(int v) const {
@@ -535,7 +534,9 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
-    PairDecoder<QC, DC, EXACT, I8, VN> dec{g, sg, gp, pc, Rb};
+    // QC codes of check degree 7 or 8 run the all-row-block pass (the row
+    // block's shifts read from the tables, not held in registers)
+    PairDecoder<QC, DC, EXACT, I8, VN, QC && DC == 8 && !EXACT> dec{g, sg, gp, pc, Rb};
 
     const long long total = (long long)b.ctr->n_cand_total;
     const long long end = b.cand_end < 0 || b.cand_end > total ? total : b.cand_end;
@@ -669,8 +670,10 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         const unsigned kb = pc.B2 & ~km;
         const bool wr = (H[0].idx >= 0 && H[0].k < misc->K[0]) || (H[1].idx >= 0 && H[1].k < misc->K[1]);
         // u_k of both halves from P_k = Pc; Pn accumulates P_{k+1}
+        // (the common form -- no half starting, messages written -- compiled with writeR constant)
         const int us = km != 0xFFFFFFFFu ? dec.template check_pass<true>(km, kb, wr, Pc, Pn)
-                                         : dec.template check_pass<false>(km, kb, wr, Pc, Pn);
+                       : wr              ? dec.template check_pass<false>(km, kb, true, Pc, Pn)
+                                         : dec.template check_pass<false>(km, kb, false, Pc, Pn);
         int restart[2] = {0, 0};
         for (int hh = 0; hh < 2; hh++) {
             Half &h = H[hh];
@@ -769,8 +772,8 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
 }
 
 template <bool QC, int DC, bool EXACT, bool I8>
-__global__ void __launch_bounds__(32 * kPairWarps) pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay,
-                                                   int G) {
+__global__ void __launch_bounds__(32 * pair_kernel_warps(QC, DC, EXACT))
+    pair_kernel(DevCode g, DecodeParams dp, EnumBuffers b, SlotLayout lay, int G) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SGraph sg = load_tables(g, smem, true);
     __syncthreads();

@@ -138,8 +138,10 @@ __global__ void __launch_bounds__(QC && DC > 8 ? 32 * kIsWarps : 512) is_kernel(
         const unsigned km = (first[0] ? 0xFFFF0000u : 0xFFFFFFFFu) & (first[1] ? 0x0000FFFFu : 0xFFFFFFFFu);
         const unsigned kb = pc.B2 & ~km;
         const bool wr = (sidx[0] >= 0 && k[0] < dp.K) || (sidx[1] >= 0 && k[1] < dp.K);
+        // (the common form -- no half starting, messages written -- compiled with writeR constant)
         const int us = km != 0xFFFFFFFFu ? dec.template check_pass<true>(km, kb, wr, Pc, Pn)
-                                         : dec.template check_pass<false>(km, kb, wr, Pc, Pn);
+                       : wr              ? dec.template check_pass<false>(km, kb, true, Pc, Pn)
+                                         : dec.template check_pass<false>(km, kb, false, Pc, Pn);
         int restart[2] = {0, 0};
         for (int hh = 0; hh < 2; hh++) {
             if (sidx[hh] < 0) continue;

@@ -75,6 +75,12 @@ constexpr int kMaxBatch = 64;
 // 20 warps keep the (3,6)-regular general-code variant at 96 registers
 // without spills and measured faster than 16 or 24
 constexpr int kPairWarps = 20;
+// QC codes and general codes of check degree 7 or 8: 16 warps a CTA (128
+// registers a thread, which those variants need to run without spilling)
+constexpr int kPairWarps16 = 16;
+__host__ __device__ constexpr int pair_kernel_warps(bool qc, int dc, bool exact) {
+    return qc || (dc == 8 && !exact) ? kPairWarps16 : kPairWarps;
+}
 // warps per CTA of the importance-sampling kernel's flat form (its launch bound)
 constexpr int kIsWarps = 18;
 struct BatchArgs {

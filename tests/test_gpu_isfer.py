@@ -36,17 +36,21 @@ def test_oracle_philox_equals_curand(tmp_path):
         assert np.array_equal(oracle.philox4x32_10(ctr[i], key[i]), out[i]), i
 
 
-def _first_ts(code, **p):
-    c = tsx.load_code(code)
-    v = tsx.ts_list_view(tsx.enumerate_ts(c, **p))
-    i = int(np.argmin(v["thr"]))
-    return c, list(v["keys"][i])
+def _first_ts(code, n_cand, **p):
+    # the biased set T: the oracle's lowest-threshold trapping set over the
+    # first n_cand canonical candidates (an input of both sides, so it comes
+    # from the oracle)
+    g = oracle.Graph(code)
+    cands = g.candidates(p.get("max_size", 3), 0)[:n_cand]
+    res = g.enumerate(cands, **p)
+    t = min(res.ts_list, key=lambda t: (t.thr, t.a, t.key))
+    return tsx.load_code(code), list(t.key)
 
 
 @pytest.mark.parametrize("ebn0,mu", [(3.0, 1.0), (2.0, 0.0), (4.5, 0.7)])
 def test_isfer_qc96_bit_exact(ebn0, mu):
     w = synth.workload("qc96")
-    c, T = _first_ts(w["code"], K=20, base_llr=16, amp_steps=10, max_size=2)
+    c, T = _first_ts(w["code"], 10**6, K=20, base_llr=16, amp_steps=10, max_size=2)
     N = 3000
     r = tsx.is_fer_estimate(c, T, ebn0_db=ebn0, mu=mu, n_samples=N, job_key=77, K=20, record=True)
     fail, logw = oracle.Graph(w["code"]).is_samples(T, ebn0_db=ebn0, mu=mu, job=77, n=N, K=20)
@@ -62,7 +66,7 @@ def test_isfer_qc96_bit_exact(ebn0, mu):
 def test_isfer_peg1008_full_size_sampled():
     # 10^6 samples on the PEG code; a window of samples checked against the oracle
     w = synth.workload("peg1008")
-    c, T = _first_ts(w["code"], K=w["K"], base_llr=16, amp_steps=w["amp_steps"], max_size=2, cand_end=20000)
+    c, T = _first_ts(w["code"], 1100, K=w["K"], base_llr=16, amp_steps=w["amp_steps"], max_size=2)
     N = 1_000_000
     r = tsx.is_fer_estimate(c, T, ebn0_db=4.0, mu=1.0, n_samples=N, job_key=9, K=w["K"], record=True)
     assert r["n_samples"] == N and r["decodes"] == N
@@ -78,3 +82,18 @@ def test_isfer_peg1008_full_size_sampled():
     assert np.array_equal(r2["logw"], r["logw"][654321:655321])
     want = float(np.sum(r["fail"] * np.exp(r["logw"]))) / N
     assert abs(r["fer"] - want) <= 1e-9 * max(want, 1e-300)
+
+
+def test_isfer_flat_form_full_size_sampled():
+    # the n = 8,832 QC code (3 x 23 all-ones base, Z = 384, check degree 23):
+    # the sampling kernel's all-row-block check pass with two checks a thread
+    code = synth.serving_codes(2026, 8)[4]
+    c, T = _first_ts(code, 40, K=20, base_llr=16, amp_steps=10, max_size=2)
+    N = 200_000
+    r = tsx.is_fer_estimate(c, T, ebn0_db=3.5, mu=1.0, n_samples=N, job_key=31, K=20, record=True)
+    assert r["n_samples"] == N and 0 < r["fail"].sum() < N
+    g = oracle.Graph(code)
+    for s0 in (0, 123457, N - 60):
+        fail, logw = g.is_samples(T, ebn0_db=3.5, mu=1.0, job=31, s0=s0, n=60, K=20)
+        assert np.array_equal(r["fail"][s0:s0 + 60], fail), s0
+        assert np.array_equal(r["logw"][s0:s0 + 60], logw), s0
