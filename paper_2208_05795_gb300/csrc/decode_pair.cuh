@@ -206,6 +206,58 @@ struct PairDecoder {
         return (int)((unsat >> 15) & 0x00010001u);
     }
 
+    // check-regular codes (EXACT, 16-bit storage, DC even): the check's DC
+    // message words are contiguous (check-major layout, 4 DC bytes a check;
+    // for QC codes within each row block) and move as DC/2 8-byte accesses;
+    // a warp's 8-byte accesses at a stride of 4 DC bytes = 24 bytes (DC = 6)
+    // touch every bank once per half-warp.  Otherwise the same steps as
+    // check_node_regs.
+    template <bool MASK, class PV>
+    __device__ __forceinline__ int check_node_cm(int rbyte, unsigned km, unsigned kb, bool writeR,
+                                                 const unsigned char *Pc, unsigned char *Pn, PV pv) const {
+        static_assert(EXACT && !I8 && DC % 2 == 0, "check-major form");
+        uint2 *rw = (uint2 *)(Rb + rbyte);
+        unsigned ys[DC];
+#pragma unroll
+        for (int t = 0; t < DC / 2; t++) {
+            const uint2 w = rw[t];
+            ys[2 * t] = w.x;
+            ys[2 * t + 1] = w.y;
+        }
+        unsigned sp = 0, sx = 0, m1 = pc.BS2, m2 = pc.BS2;
+        unsigned qs[DC], as_[DC];
+        int po[DC];
+#pragma unroll
+        for (int p = 0; p < DC; p++) {
+            po[p] = pv(p);
+            const unsigned x = *(const unsigned *)(Pc + po[p]);
+            const unsigned y = MASK ? ((ys[p] & km) | kb) : ys[p];
+            sp ^= x;
+            unsigned q, a;
+            edge_da(x, y, q, a);
+            sx ^= q;
+            m2 = vminu2(m2, vmaxu2(m1, a));
+            m1 = vminu2(m1, a);
+            qs[p] = q;
+            as_[p] = a;
+        }
+        const unsigned unsat = (sp ^ ((DC & 1) ? 0x80008000u : 0u)) & 0x80008000u;
+        if (writeR) {
+            const unsigned o1 = ((m1 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
+            const unsigned o2 = ((m2 * (unsigned)pc.an - pc.BAN2) >> pc.as) & pc.amask2;
+            const Outs oo = outs(o1, o2);
+            const unsigned sxk = sx ^ (((DC - 1) & 1) ? 0x80008000u : 0u);
+#pragma unroll
+            for (int p = 0; p < DC; p++) ys[p] = edge_out(qs[p], as_[p], m1, oo, sxk);
+#pragma unroll
+            for (int t = 0; t < DC / 2; t++) rw[t] = make_uint2(ys[2 * t], ys[2 * t + 1]);
+#pragma unroll
+            for (int p = 0; p < DC; p++)
+                if constexpr (!VN) red_add(Pn + po[p], ys[p]);
+        }
+        return (int)((unsat >> 15) & 0x00010001u);
+    }
+
     // large degree: the first pass leaves each edge's q'' in its message slot
     // (16-bit storage: a slot holds both halves' q''), the second reads it
     // back; with 8-bit storage the second pass reloads P and recomputes q
@@ -371,8 +423,13 @@ struct PairDecoder {
                             const int t = r + rsh[p];
                             return rjz4[p] + 4 * (int)min((unsigned)t, (unsigned)(t - Z));
                         };
-                        u += check_node<MASK>(deg, km, kb, writeR, Pc, Pn, pv,
-                                              [&](int p) { return rb + pz[p] + r * RSZ; });
+                        if constexpr (EXACT && !I8 && DC % 2 == 0) {
+                            // check-regular row blocks: messages check-major within the block
+                            u += check_node_cm<MASK>(rb + r * (DC * RSZ), km, kb, writeR, Pc, Pn, pv);
+                        } else {
+                            u += check_node<MASK>(deg, km, kb, writeR, Pc, Pn, pv,
+                                                  [&](int p) { return rb + pz[p] + r * RSZ; });
+                        }
                     }
                 } else {
                     const int32_t *rjz = sg.rjz + i * g.dc_max;
@@ -396,6 +453,13 @@ struct PairDecoder {
                         u += f;
                     }
                 }
+            }
+        } else if constexpr (EXACT && !I8 && DC % 2 == 0) {
+            // check-regular: rows of DC edges, messages check-major
+            for (int c = gp.gt; c < g.m; c += gp.T) {
+                const int e0 = c * DC;
+                u += check_node_cm<MASK>(e0 * RSZ, km, kb, writeR, Pc, Pn,
+                                         [&](int p) { return 4 * (int)sg.c_vn[e0 + p]; });
             }
         } else {
             const int m = g.m;
