@@ -694,11 +694,23 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         h.first = 1;
     };
     // impulse nodes: the current posteriors (new decode only) and the accumulator
-    auto patch = [&](Half &h, int hh, unsigned *Pc, unsigned *Pn, bool cur_too) {
-        if (h.idx >= 0 && gp.gt < h.nI) {
-            const int t = h.Ik(gp.gt);
-            if (cur_too) dec.set_half(Pc, t, hh, (unsigned)(h.Limp + (int)kBeta));
-            dec.set_half(Pn, t, hh, (unsigned)(h.Limp + (int)kBeta - dec.vdeg(t) * pc.B));
+    // the impulse nodes of a new decode in the current posteriors
+    auto patch_cur = [&](Half &h, int hh, unsigned *Pc) {
+        if (h.idx >= 0 && gp.gt < h.nI) dec.set_half(Pc, h.Ik(gp.gt), hh, (unsigned)(h.Limp + (int)kBeta));
+    };
+    // The accumulator starts at the baseline L' in every word; its impulse
+    // nodes get L_imp - L_base added in their half with the check pass's
+    // red.adds (threads 0-3: half 0, 4-7: half 1).  The adds are exact and
+    // commute: the word's final halves are in range, so no intermediate
+    // carry or borrow between the halves survives.
+    auto impulse_adds = [&](unsigned *Pn) {
+        if (gp.gt < 8) {  // (the halves selected by value: H stays in registers)
+            const int j = gp.gt & 3;
+            const bool h1 = gp.gt >= 4;
+            const bool on = h1 ? H[1].idx >= 0 && j < H[1].nI : H[0].idx >= 0 && j < H[0].nI;
+            const int t = h1 ? H[1].Ik(j) : H[0].Ik(j);
+            const unsigned d = (unsigned)((h1 ? H[1].Limp : H[0].Limp) - Lb);
+            if (on) red_add((unsigned char *)(Pn + t), h1 ? d << 16 : d);
         }
     };
 
@@ -723,7 +735,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         gp.sync();
         for (int hh = 0; hh < 2; hh++) {
             if constexpr (VN) patch_vn(H[hh], hh, Pc, true);
-            else patch(H[hh], hh, Pc, Pn, true);
+            else patch_cur(H[hh], hh, Pc);
         }
         gp.sync();
     }
@@ -734,11 +746,13 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         const unsigned kb = pc.B2 & ~km;
         const bool wr = (H[0].idx >= 0 && H[0].k < misc->K[0]) || (H[1].idx >= 0 && H[1].k < misc->K[1]);
         // u_k of both halves from P_k = Pc; Pn accumulates P_{k+1}
+        if constexpr (!VN) impulse_adds(Pn);
         // (the common form -- no half starting, messages written -- compiled with writeR constant)
         const int us = km != 0xFFFFFFFFu ? dec.template check_pass<true>(km, kb, wr, Pc, Pn)
                        : wr              ? dec.template check_pass<false>(km, kb, true, Pc, Pn)
                                          : dec.template check_pass<false>(km, kb, false, Pc, Pn);
         int restart[2] = {0, 0};
+        bool read_pc = false;  // some thread read P_k after the check pass (uniform)
         for (int hh = 0; hh < 2; hh++) {
             Half &h = H[hh];
             if (h.idx < 0) continue;
@@ -747,8 +761,10 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
             if (h.k >= g.wstart && u < h.ubest) {
                 h.ubest = u;
                 dec.save_x(Pc, hh, xc);
+                read_pc = true;
             }
             if (u != 0 && h.k != misc->K[hh]) continue;
+            read_pc = true;
             // the decode ended at K_last = k
             const int kl = h.k;
             if (kl < g.wstart) dec.save_x(Pc, hh, xc);
@@ -809,8 +825,9 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
             gp.sync();
             continue;
         }
-        // Pn (= P_{k+1}) becomes current; the old Pc becomes the next accumulator
-        gp.sync();
+        // Pn (= P_{k+1}) becomes current; the old Pc becomes the next
+        // accumulator (a barrier first if P_k was read after the check pass)
+        if (read_pc) gp.sync();
         for (int hh = 0; hh < 2; hh++) {
             Half &h = H[hh];
             if (restart[hh]) {
@@ -821,8 +838,11 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
             }
         }
         dec.init_accum(Pc, Lb);
-        gp.sync();
-        for (int hh = 0; hh < 2; hh++) patch(H[hh], hh, Pn, Pc, restart[hh] != 0);
+        if (restart[0] | restart[1]) {
+            gp.sync();  // after start_cur's stores
+            for (int hh = 0; hh < 2; hh++)
+                if (restart[hh]) patch_cur(H[hh], hh, Pn);
+        }
         gp.sync();
         pcur ^= 1;
     }
