@@ -134,12 +134,17 @@ struct PairDecoder {
         q = vminu2(vmaxu2(x - y + pc.B2, pc.LO2), pc.HI2);
         a = vmaxu2(q, (~q) + 0x00010001u);
     }
-    // the same without clamping the value: d = (P - r) + beta, which the
-    // launcher's bounds keep inside each half and which has the sign of
-    // clamp(P - r), and a = min(|P - r|, sat) + beta, the clamped magnitude
+    // the same without clamping: d = (P - r) + beta, which the launcher's
+    // bounds keep inside each half and which has the sign of clamp(P - r),
+    // and a = |P - r| + beta.  Where |P - r| > sat the clamped magnitude
+    // would be sat: min1 and min2 start at sat (+ beta), so they come out
+    // the same, and such an edge's output is the same too -- it is not the
+    // minimum unless min1 = min2 = sat, when both outputs are equal.
+    // |P - r| <= sat + (dv - 1) B < 2^15 by the launcher's bounds, so
+    // a - min1 + 0x7FFF stays inside each half, as edge_out needs.
     __device__ __forceinline__ void edge_da(unsigned x, unsigned y, unsigned &d, unsigned &a) const {
         d = x - y + pc.B2;
-        a = vminu2(vmaxu2(d, (~d) + 0x00010001u), pc.BS2);
+        a = vmaxu2(d, (~d) + 0x00010001u);
     }
 
     // the new message of an edge from its q'', |q|, the check's min1, the
