@@ -361,19 +361,21 @@ def _arr(ptr, n, dtype):
     return np.ctypeslib.as_array(ptr, shape=(n,)).astype(dtype, copy=True)
 
 
-def ts_list_view(lst: TsList, check: bool = True) -> dict:
+def ts_list_view(lst: TsList, check: bool = True, keys: bool = True) -> dict:
     """Synchronizes, copies the results out; returns numpy arrays:
-    per TS: a, b, orbit, count, thr, thr_f, flags, keys (list of tuples);
-    per candidate: cand_vars [N,4], cand_thr, cand_thr_f, cand_ts,
-    cand_flags, cand_decodes, cand_iters; and stats."""
+    per TS: a, b, orbit, count, thr, thr_f, flags, the canonical keys as
+    key_vars (concatenated) with key_off [n_ts + 1], and with keys=True also
+    keys (a list of tuples, built on the host); per candidate: cand_vars
+    [N,4], cand_thr, cand_thr_f, cand_ts, cand_flags, cand_decodes,
+    cand_iters; and stats."""
     v = TsView()
     st = lib().ts_list_view(lst.h, C.byref(v))
     if check:
         _check(st, "ts_list_view")
-    return _view_dict(v, st)
+    return _view_dict(v, st, keys)
 
 
-def _view_dict(v, st) -> dict:
+def _view_dict(v, st, keys=True) -> dict:
     nts, nc = int(v.n_ts), int(v.n_cand)
     out = {"status": st, "stats": {k: getattr(v.stats, k) for k, _ in EnumStats._fields_}}
     for k in ("a", "b", "orbit", "count", "thr", "flags"):
@@ -381,7 +383,10 @@ def _view_dict(v, st) -> dict:
     out["thr_f"] = _arr(v.thr_f, nts, np.float32)
     off = _arr(v.var_off, nts + 1, np.int64) if nts else np.zeros(1, np.int64)
     vars_ = _arr(v.vars, int(off[-1]), np.int32)
-    out["keys"] = [tuple(int(x) for x in vars_[off[i]:off[i + 1]]) for i in range(nts)]
+    out["key_vars"], out["key_off"] = vars_, off
+    if keys:
+        flat, o = vars_.tolist(), off.tolist()
+        out["keys"] = [tuple(flat[o[i]:o[i + 1]]) for i in range(nts)]
     out["cand_vars"] = _arr(v.cand_vars, 4 * nc, np.int32).reshape(nc, 4)
     for k in ("cand_thr", "cand_ts", "cand_flags", "cand_decodes", "cand_iters"):
         out[k] = _arr(getattr(v, k), nc, np.int32)
@@ -458,12 +463,12 @@ def batch_run(batch: Batch, stream=None):
     _check(lib().batch_run(batch.h, _stream_handle(stream)), "batch_run")
 
 
-def batch_view(batch: Batch, i: int, check: bool = True) -> dict:
+def batch_view(batch: Batch, i: int, check: bool = True, keys: bool = True) -> dict:
     v = TsView()
     st = lib().batch_view(batch.h, int(i), C.byref(v))
     if check:
         _check(st, "batch_view")
-    return _view_dict(v, st)
+    return _view_dict(v, st, keys)
 
 
 def batch_stats(batch: Batch, check: bool = True) -> dict:
@@ -593,12 +598,12 @@ class Server:
             _check(st, "server_wait")
         return _struct_dict(r)
 
-    def view(self, jid: int, check: bool = True) -> dict:
+    def view(self, jid: int, check: bool = True, keys: bool = True) -> dict:
         v = TsView()
         st = lib().server_job_view(self.h, jid, C.byref(v))
         if check:
             _check(st, "server_job_view")
-        return _view_dict(v, st)
+        return _view_dict(v, st, keys)
 
     def release(self, jid: int):
         _check(lib().server_release(self.h, jid), "server_release")
