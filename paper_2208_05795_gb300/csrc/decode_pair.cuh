@@ -13,9 +13,10 @@
 //   message   R' = r + B                     B = 1024 (int16) / 128 (int8)
 //   posterior P' = P + beta                  beta = 0x8000
 //   channel   L'(v) = L_v + beta - dv(v) B   so P' = L' + sum_c R'
-//   extrinsic q'' = clamp(P' - R' + B) = clamp(q) + beta, clamped to [beta - sat, beta + sat]
-//                                           (one three-input add, then min/max): bit 15 of each half is [q >= 0]
-//   magnitude a = max(q'', 2 beta - q'') = |q| + beta   (2 beta - x = ~x + 1 per half)
+//   extrinsic d = P' - R' + B = q + beta     (one three-input add): bit 15 of each half is
+//                                           [q >= 0], the sign of clamp(q); the clamp itself
+//                                           is not applied (edge_da says why it changes nothing)
+//   magnitude a = max(d, 2 beta - d) = |q| + beta   (2 beta - x = ~x + 1 per half)
 // Every intermediate stays inside [0, 0xFFFF] per half for rmax <= B and
 // (dv + 2) sat <= beta - B, which the launcher checks; both halves always
 // hold values of a valid decode (an idle half keeps decoding its last input)
@@ -63,7 +64,7 @@ __device__ __forceinline__ void red_add(unsigned char *addr, unsigned v) {
 constexpr unsigned kBeta = 0x8000u;
 
 struct PairConst {
-    unsigned B2, BS2, LO2, HI2, BETA2, amask2;  // LO2 / HI2: clamp bounds of q'' = q + beta
+    unsigned B2, BS2, BETA2, amask2;
     unsigned BAN2;  // BETA2 * alpha_num: (m - beta) an = m an - BAN2 (mod 2^32)
     int B, sat, an, as;
 };
@@ -129,12 +130,7 @@ struct PairDecoder {
         else return check_node_twopass<MASK>(deg, km, kb, writeR, Pc, Pn, pv, re);
     }
 
-    // extrinsic value q'' = clamp(q) + beta and magnitude |q| + beta of one edge
-    __device__ __forceinline__ void edge_q(unsigned x, unsigned y, unsigned &q, unsigned &a) const {
-        q = vminu2(vmaxu2(x - y + pc.B2, pc.LO2), pc.HI2);
-        a = vmaxu2(q, (~q) + 0x00010001u);
-    }
-    // the same without clamping: d = (P - r) + beta, which the launcher's
+    // the extrinsic value of one edge without clamping: d = (P - r) + beta, which the launcher's
     // bounds keep inside each half and which has the sign of clamp(P - r),
     // and a = |P - r| + beta.  Where |P - r| > sat the clamped magnitude
     // would be sat: min1 and min2 start at sat (+ beta), so they come out
@@ -263,9 +259,10 @@ struct PairDecoder {
         return (int)((unsat >> 15) & 0x00010001u);
     }
 
-    // large degree: the first pass leaves each edge's q'' in its message slot
-    // (16-bit storage: a slot holds both halves' q''), the second reads it
-    // back; with 8-bit storage the second pass reloads P and recomputes q
+    // large degree: the first pass leaves each edge's extrinsic word d in its
+    // message slot (16-bit storage: a slot holds both halves' d), the second
+    // reads it back; with 8-bit storage the second pass reloads P and
+    // recomputes d
     template <bool MASK, class PV, class RE>
     __device__ __forceinline__ int check_node_twopass(int deg, unsigned km, unsigned kb, bool writeR,
                                                       const unsigned char *Pc, unsigned char *Pn, PV pv,
@@ -278,7 +275,7 @@ struct PairDecoder {
             const unsigned y = ldy<MASK>(ro, km, kb);
             sp ^= x;
             unsigned q, a;
-            edge_q(x, y, q, a);
+            edge_da(x, y, q, a);
             if constexpr (!I8)
                 if (writeR) stR(ro, q);
             sx ^= q;
@@ -302,7 +299,7 @@ struct PairDecoder {
                 } else {
                     const unsigned x = *(const unsigned *)(Pc + po);
                     const unsigned y = ldy<MASK>(ro, km, kb);
-                    edge_q(x, y, q, a);
+                    edge_da(x, y, q, a);
                 }
                 const unsigned rn = edge_out(q, a, m1, oo, sxk);
                 stR(ro, rn);
@@ -337,8 +334,8 @@ struct PairDecoder {
             spA ^= xA;
             spB ^= xB;
             unsigned qA, aA, qB, aB;
-            edge_q(xA, yA, qA, aA);
-            edge_q(xB, yB, qB, aB);
+            edge_da(xA, yA, qA, aA);
+            edge_da(xB, yB, qB, aB);
             if (writeR) {
                 stR(roA, qA);
                 stR(roB, qB);
@@ -599,8 +596,6 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
     pc.B2 = (unsigned)pc.B * 0x00010001u;
     pc.BETA2 = kBeta * 0x00010001u;
     pc.BS2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
-    pc.LO2 = (kBeta - (unsigned)pc.sat) * 0x00010001u;
-    pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
     // QC codes of check degree 7 or 8 run the all-row-block pass (the row

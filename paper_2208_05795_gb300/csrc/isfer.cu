@@ -73,11 +73,11 @@ __global__ void __launch_bounds__(QC && DC > 8 ? 32 * kIsWarps : 512) is_kernel(
     pc.B2 = (unsigned)pc.B * 0x00010001u;
     pc.BETA2 = kBeta * 0x00010001u;
     pc.BS2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
-    pc.LO2 = (kBeta - (unsigned)pc.sat) * 0x00010001u;
-    pc.HI2 = (kBeta + (unsigned)pc.sat) * 0x00010001u;
     pc.amask2 = (0xFFFFu >> pc.as) * 0x00010001u;
     pc.BAN2 = pc.BETA2 * (unsigned)pc.an;
-    PairDecoder<QC, DC, EXACT, false, false, QC && (DC > 8)> dec{g, sg, gp, pc, Rb};
+    // QC codes: the all-row-block pass for check degree > 8 (wider groups) and for
+    // degree 7-8 (the row block's shifts read from the tables, not held in registers)
+    PairDecoder<QC, DC, EXACT, false, false, QC && (DC > 8 || !EXACT)> dec{g, sg, gp, pc, Rb};
 
     for (int w = gp.gt; w < nw; w += gp.T) Tm[w] = 0u;
     gp.sync();
@@ -133,7 +133,13 @@ __global__ void __launch_bounds__(QC && DC > 8 ? 32 * kIsWarps : 512) is_kernel(
     }
     while (sidx[0] >= 0 || sidx[1] >= 0) {
         unsigned *Pc = Pbuf + pcur * g.n, *Pn = Pbuf + (pcur ^ 1) * g.n;
-        for (int v = gp.gt; v < g.n; v += gp.T) Pn[v] = L2[v];
+        if ((g.n & 3) == 0) {  // 16-byte copies (Pbuf is 16-byte aligned, so are Pn and L2)
+            const uint4 *src = (const uint4 *)L2;
+            uint4 *dst = (uint4 *)Pn;
+            for (int q = gp.gt; q < (g.n >> 2); q += gp.T) dst[q] = src[q];
+        } else {
+            for (int v = gp.gt; v < g.n; v += gp.T) Pn[v] = L2[v];
+        }
         gp.sync();
         const unsigned km = (first[0] ? 0xFFFF0000u : 0xFFFFFFFFu) & (first[1] ? 0x0000FFFFu : 0xFFFFFFFFu);
         const unsigned kb = pc.B2 & ~km;
