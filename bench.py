@@ -54,7 +54,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
-from paper_2208_05795_gb300.shard import reduce_time_and_work  # noqa: E402
+from paper_2208_05795_gb300.shard import exchange, reduce_time_and_work, shard_bounds, ts_records  # noqa: E402
 
 # integer operations the min-sum edge update needs at minimum: |q|, two
 # compare-selects for min1/min2, argmin select, sign xor, output select,
@@ -136,6 +136,10 @@ def parse():
                     help="decode only the first N canonical candidates (profiling a bounded case)")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only (no extra workloads)")
     ap.add_argument("--procs", type=int, default=0, help="oracle processes (0 = every host core)")
+    ap.add_argument("--split", action="store_true",
+                    help="several ranks: split one code's canonical candidate list into contiguous ranges "
+                         "(strong scaling) and merge the per-range trapping sets in one exchange step, "
+                         "instead of one independent code per rank")
     return ap.parse_args()
 
 
@@ -345,7 +349,8 @@ def run_ours(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     tsx_build.build()
     pk = tsx.measure_peaks()
-    w = workload_for(args.workload, rank)
+    split = args.split and world > 1
+    w = workload_for(args.workload, 0 if split else rank)
     params = params_of(w, args.decoder)
     if args.decoder == "nms8":
         params["sat"] = 127
@@ -353,6 +358,14 @@ def run_ours(args):
         params["cand_end"] = args.cand_limit
     stream = torch.cuda.Stream()
     code = tsx.load_code(w["code"], stream=stream)
+    shard_range, shard_n_total = None, 0
+    if split:
+        # this rank's contiguous range of the one code's canonical list
+        n_total = tsx.ts_list_stats(tsx.enumerate_ts(code, stream=stream, **dict(params, cand_end=0)))["n_cand_total"]
+        if args.cand_limit >= 0:
+            n_total = min(n_total, args.cand_limit)
+        shard_range, shard_n_total = shard_bounds(n_total, rank, world), n_total
+        params.update(cand_begin=shard_range[0], cand_end=shard_range[1])
     info = code.info
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     has_cycles = w["cycle_len"] // 2 > w["max_size"]
@@ -418,6 +431,14 @@ def run_ours(args):
         e2e = {"value": eu2 / wall, "unit": "edge-updates/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    split_info = None
+    if split:
+        # the one exchange step: every range's (key -> record) map, merged by key on every rank
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        merged = exchange(ts_records(tsx.ts_list_view(step())))
+        split_info = {"ranks": world, "cand_range_rank0": list(shard_range), "n_ts_merged": len(merged),
+                      "ms_view_and_exchange": 1e3 * (time.perf_counter() - t0)}
     if rank != 0:
         if dist:
             dist.barrier()
@@ -447,17 +468,18 @@ def run_ours(args):
         "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if split else "weak",
         "vs_baseline": None,
         "dtype": "f32" if args.decoder == "spa" else ("int8" if args.decoder == "nms8" else "int16"),
         "data": "synthetic",
         "config": {"workload": args.workload + (f"[:{args.cand_limit}]" if args.cand_limit >= 0 else ""),
                    "decoder": args.decoder, "n": info["n"], "m": info["m"],
                    "E": info["E"], "girth": info["girth"], "K": w["K"], "amp_steps": w["amp_steps"],
-                   "base_llr": w["base_llr"], "n_cand": int(s["n_cand"]), "parallelism": f"replicas{world}",
+                   "base_llr": w["base_llr"], "n_cand": int(shard_n_total if split else s["n_cand"]),
+                   "parallelism": f"split{world}" if split else f"replicas{world}",
                    "l2": "flushed before each step (256 MB write)"},
         "decodes_per_s": dec_all / (total_ms / 1e3),
-        "distinct_ts_per_s": nts * world / (total_ms / args.steps / 1e3),
+        "distinct_ts_per_s": (split_info["n_ts_merged"] if split else nts * world) / (total_ms / args.steps / 1e3),
         "n_ts": nts,
         "ms_decode_kernel": avg_dec_ms,
         "ms_candidates": sum(ms_cand) / len(ms_cand),
@@ -468,6 +490,8 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
     }
+    if split_info:
+        line["split"] = split_info
     if extras:
         line["extra"] = extras
     print(json.dumps(line), flush=True)

@@ -615,7 +615,7 @@ __device__ void pair_run(const DevCode &g, const DecodeParams &dp, const EnumBuf
         misc->okit = 0;
     }
 
-    Half H[2];
+    Half H[2] = {};  // (every field is set by fetch before use)
 
     auto fetch = [&](Half &h, int hh) {
         if (gp.gt == 0) misc->bcast[0] = (long long)atomicAdd(b.queue, 1ull);
