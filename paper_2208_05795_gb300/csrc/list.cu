@@ -46,9 +46,12 @@ ListLayout list_layout(const DevCode &g, int K) {
 }
 
 constexpr int kSmemCta = 226 * 1024;
+// up to 20 warps a CTA: the second stage is latency and barrier bound, and
+// one group more than 16 warps allow fits the shared memory of the QC codes
+constexpr int kListWarps = 20;
 
 template <int DCMAX, bool QC>
-__global__ void __launch_bounds__(512) list_kernel(DevCode g, DecodeParams dp, EnumBuffers b, ListLayout lay, int G,
+__global__ void __launch_bounds__(32 * kListWarps) list_kernel(DevCode g, DecodeParams dp, EnumBuffers b, ListLayout lay, int G,
                                                     int kstart_req) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SGraph sg = load_tables(g, smem);
@@ -194,7 +197,7 @@ bool list_shape(const DevCode &g, int K, ListShape *sh) {
     int G = work / 256;
     if (G < 1) G = 1;
     if (G > 4) G = 4;
-    int groups = 16 / G;
+    int groups = kListWarps / G;
     if (groups > fit) groups = fit;
     if (G > 1 && groups > 15) groups = 15;
     sh->G = G;
