@@ -960,7 +960,7 @@ __device__ __forceinline__ void scalar_run(const DevCode &g, const DecodeParams 
 }
 
 template <class Dec, int DCMAX, bool QC>
-__global__ void __launch_bounds__(512) enum_kernel(DevCode g, DecodeParams dp, EnumBuffers b,
+__global__ void __launch_bounds__(512, 1) enum_kernel(DevCode g, DecodeParams dp, EnumBuffers b,
                                                     SlotLayout lay, int G) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SGraph sg = load_tables(g, smem);

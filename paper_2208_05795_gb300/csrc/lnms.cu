@@ -69,7 +69,7 @@ __device__ __forceinline__ int round_half_away(float x, int lim) {
 }
 
 template <int DCMAX>
-__global__ void __launch_bounds__(512) lnms_kernel(DevCode g, LnmsArgs a, LnmsLayout lay, int G) {
+__global__ void __launch_bounds__(512, 1) lnms_kernel(DevCode g, LnmsArgs a, LnmsLayout lay, int G) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SGraph sg = load_tables(g, smem);
     __syncthreads();
