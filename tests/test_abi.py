@@ -50,3 +50,36 @@ def test_binding_marshals_without_gpu(libpath):
     assert (q.decoder, q.K, q.amp_steps) == (2, 50, 12)
     with pytest.raises(TypeError):
         tsx.make_params(bogus=1)
+
+
+def test_view_marshalling_keys_as_arrays_and_tuples():
+    # the binding's copy of a ts_list_view() result (no library call): the
+    # canonical keys come back as one concatenated array with offsets, and
+    # with keys=True also as tuples equal to the slices
+    import numpy as np
+    from paper_2208_05795_gb300 import _tsx
+
+    def ptr(a, t):
+        return a.ctypes.data_as(ctypes.POINTER(t))
+
+    off = np.array([0, 3, 3, 7], np.int64)  # a set of size 0 is kept as an empty key
+    vars_ = np.array([5, 9, 11, 0, 2, 4, 1000], np.int32)
+    per_ts = {k: np.arange(3, dtype=np.int32) + i for i, k in enumerate(("a", "b", "orbit", "count", "thr", "flags"))}
+    thr_f = np.array([0.5, -1.0, 2.0], np.float32)
+    cand = np.arange(8, dtype=np.int32)
+    v = _tsx.TsView()
+    v.n_ts, v.n_cand = 3, 2
+    for k, arr in per_ts.items():
+        setattr(v, k, ptr(arr, ctypes.c_int32))
+    v.thr_f, v.var_off, v.vars = ptr(thr_f, ctypes.c_float), ptr(off, ctypes.c_int64), ptr(vars_, ctypes.c_int32)
+    v.cand_vars = ptr(cand, ctypes.c_int32)
+    for k in ("cand_thr", "cand_ts", "cand_flags", "cand_decodes", "cand_iters"):
+        setattr(v, k, ptr(cand, ctypes.c_int32))
+    v.cand_thr_f = ptr(thr_f, ctypes.c_float)
+    with_keys = _tsx._view_dict(v, 0, True)
+    without = _tsx._view_dict(v, 0, False)
+    assert with_keys["keys"] == [(5, 9, 11), (), (0, 2, 4, 1000)]
+    assert "keys" not in without
+    for d in (with_keys, without):
+        assert np.array_equal(d["key_vars"], vars_) and np.array_equal(d["key_off"], off)
+        assert np.array_equal(d["orbit"], per_ts["orbit"]) and d["cand_vars"].shape == (2, 4)
